@@ -1,0 +1,189 @@
+"""Plain FP64 CPU oracle for truncated-LJ molecular dynamics (ctypes wrapper).
+
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT: only the test suite, the
+package's smoke check and the benchmark's CPU-baseline leg use it. It shares
+no code with the CUDA path and never imports it.
+
+Every function follows the paper (Watanabe, Suzuki, Ito, arXiv:1210.3450):
+Eq. 1 for the truncated potential, Sec. 2.1 for the cell search and the
+bookkeeping list, Algorithm 1 (Sec. 3.3) for the full-list force factor, and
+the second-order symplectic (velocity Verlet) update of Sec. 3.2 / 4.1.
+The arithmetic lives in ``ljmd_oracle.c``; this module only marshals arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .build import build as _build
+
+_lib = None
+
+_D = C.c_double
+_I64 = C.c_int64
+_PD = C.POINTER(C.c_double)
+_PI64 = C.POINTER(C.c_int64)
+_PI32 = C.POINTER(C.c_int32)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(_build())
+        sig = {
+            "orc_lj_coeffs": (None, [_D, _PD, _PD]),
+            "orc_pair_energy": (_D, [_D, _D, _D, _D]),
+            "orc_pair_force_factor": (_D, [_D, _D, _D]),
+            "orc_pair_virial": (_D, [_D, _D, _D]),
+            "orc_wrap": (None, [_I64, _D, _PD]),
+            "orc_cells_per_axis": (C.c_int, [_D, _D]),
+            "orc_cell_index": (None, [_I64, _D, C.c_int, _PD, _PI32]),
+            "orc_build_list": (_I64, [_I64, _D, _D, _PD, _PI64, _PI32, _I64]),
+            "orc_build_list_brute": (_I64, [_I64, _D, _D, _PD, _PI64, _PI32, _I64]),
+            "orc_forces_list": (None, [_I64, _D, _D, _D, _PD, _PI64, _PI32, _PD]),
+            "orc_force_on": (None, [_I64, _D, _D, _D, _PD, _I64, _PD]),
+            "orc_forces_brute": (None, [_I64, _D, _D, _D, _PD, _PD]),
+            "orc_observables_list": (None, [_I64, _D, _D, _D, _D, _PD, _PD, _PI64, _PI32, _PD]),
+            "orc_run": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(_PD)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def lj_coeffs(rc: float) -> tuple[float, float]:
+    """(c2, c0) of Eq. 1 from V(rc) = V'(rc) = 0."""
+    c2, c0 = _D(), _D()
+    _load().orc_lj_coeffs(rc, C.byref(c2), C.byref(c0))
+    return c2.value, c0.value
+
+
+def pair_energy(r2: float, rc: float, c2: float, c0: float) -> float:
+    return _load().orc_pair_energy(r2, rc * rc, c2, c0)
+
+
+def pair_force_factor(r2: float, rc: float, c2: float) -> float:
+    return _load().orc_pair_force_factor(r2, rc * rc, c2)
+
+
+def pair_virial(r2: float, rc: float, c2: float) -> float:
+    return _load().orc_pair_virial(r2, rc * rc, c2)
+
+
+def wrap(x, box: float) -> np.ndarray:
+    x = _f64(x, (-1, 3)).copy()
+    _load().orc_wrap(x.shape[0], box, _pd(x))
+    return x
+
+
+def cells_per_axis(box: float, rl: float) -> int:
+    return _load().orc_cells_per_axis(box, rl)
+
+
+def cell_index(x, box: float, rl: float) -> np.ndarray:
+    """Linear cell index cx + nc (cy + nc cz) of each particle (positions in [0, L))."""
+    x = _f64(x, (-1, 3))
+    nc = cells_per_axis(box, rl)
+    out = np.empty(x.shape[0], dtype=np.int32)
+    _load().orc_cell_index(x.shape[0], box, nc, _pd(x), out.ctypes.data_as(_PI32))
+    return out
+
+
+def build_list(x, box: float, rl: float, brute: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Full list {j != i : min-image r^2 < rl^2}: (start[n+1] int64, partners int32),
+    partners of each i ascending."""
+    x = _f64(x, (-1, 3))
+    n = x.shape[0]
+    start = np.empty(n + 1, dtype=np.int64)
+    cap = max(64, n * 96)
+    fn = _load().orc_build_list_brute if brute else _load().orc_build_list
+    while True:
+        partners = np.empty(cap, dtype=np.int32)
+        got = fn(n, box, rl, _pd(x), start.ctypes.data_as(_PI64), partners.ctypes.data_as(_PI32), cap)
+        if got >= 0:
+            return start, partners[:got].copy()
+        cap = -got
+
+
+def forces_list(x, box: float, rc: float, c2: float, start, partners) -> np.ndarray:
+    x = _f64(x, (-1, 3))
+    f = np.empty_like(x)
+    start = np.ascontiguousarray(start, dtype=np.int64)
+    partners = np.ascontiguousarray(partners, dtype=np.int32)
+    _load().orc_forces_list(x.shape[0], box, rc, c2, _pd(x), start.ctypes.data_as(_PI64),
+                            partners.ctypes.data_as(_PI32), _pd(f))
+    return f
+
+
+def forces(x, box: float, rc: float, skin: float = 0.3, c2: float | None = None) -> np.ndarray:
+    """Forces through the cell-built list (list radius rc + skin)."""
+    if c2 is None:
+        c2 = lj_coeffs(rc)[0]
+    start, partners = build_list(x, box, rc + skin)
+    return forces_list(x, box, rc, c2, start, partners)
+
+
+def forces_brute(x, box: float, rc: float, c2: float | None = None) -> np.ndarray:
+    if c2 is None:
+        c2 = lj_coeffs(rc)[0]
+    x = _f64(x, (-1, 3))
+    f = np.empty_like(x)
+    _load().orc_forces_brute(x.shape[0], box, rc, c2, _pd(x), _pd(f))
+    return f
+
+
+def force_on(x, box: float, rc: float, i: int, c2: float | None = None) -> np.ndarray:
+    """Force on one particle by direct summation over all others."""
+    if c2 is None:
+        c2 = lj_coeffs(rc)[0]
+    x = _f64(x, (-1, 3))
+    out = np.empty(3)
+    _load().orc_force_on(x.shape[0], box, rc, c2, _pd(x), int(i), _pd(out))
+    return out
+
+
+def observables(x, v, box: float, rc: float, skin: float = 0.3, c2=None, c0=None) -> dict:
+    """PE, virial W, KE, T = 2KE/(3(N-1)), P = (2KE + W)/(3V)."""
+    if c2 is None or c0 is None:
+        c2, c0 = lj_coeffs(rc)
+    x = _f64(x, (-1, 3))
+    v = _f64(v, (-1, 3))
+    start, partners = build_list(x, box, rc + skin)
+    out = np.empty(5)
+    _load().orc_observables_list(x.shape[0], box, rc, c2, c0, _pd(x), _pd(v),
+                                 start.ctypes.data_as(_PI64), partners.ctypes.data_as(_PI32),
+                                 _pd(out))
+    return dict(pe=out[0], virial=out[1], ke=out[2], temperature=out[3], pressure=out[4])
+
+
+def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
+        trace_every: int = 0) -> dict:
+    """Velocity-Verlet run; returns dict(x, v, rebuilds, trace)."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    rebuilds = _I64(0)
+    trace = None
+    tp = None
+    if trace_every > 0:
+        trace = np.empty(1 + nsteps // trace_every)
+        tp = _pd(trace)
+    rc_ = _load().orc_run(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt,
+                          C.byref(rebuilds), tp, trace_every)
+    if rc_ != 0:
+        raise MemoryError("oracle run failed to allocate")
+    return dict(x=x, v=v, rebuilds=rebuilds.value, trace=trace)
