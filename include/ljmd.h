@@ -1,0 +1,160 @@
+/*
+ * ljmd.h — C ABI of the GB300 truncated-Lennard-Jones molecular-dynamics library.
+ *
+ * The library integrates N particles in a cubic periodic box of side L under the
+ * truncated LJ potential of Eq. 1 of Watanabe, Suzuki and Ito, "Huge-scale
+ * Molecular Dynamics Simulation of Multibubble Nuclei" (arXiv:1210.3450):
+ *     V(r) = 4 [ r^-12 - r^-6 + c2 r^2 + c0 ]   for r < rc, 0 otherwise,
+ * with c2 = 6 rc^-14 - 3 rc^-8 and c0 = 4 rc^-6 - 7 rc^-12 so that V(rc) = V'(rc) = 0
+ * (reduced units: sigma = epsilon = k_B = m = 1). Forces come from a full Verlet
+ * pair list (radius rl = rc + skin, Sec. 2.1 "bookkeeping method") built from a cell
+ * grid (Sec. 2.1 "grid algorithm"), without Newton's third law (Sec. 3.3). The time
+ * integrator is the second-order symplectic velocity-Verlet scheme (Sec. 3.2, 4.1).
+ * The list is rebuilt when twice the largest displacement since the last build
+ * reaches the skin (the list-validity check of Sec. 2.1).
+ *
+ * Conventions for every call:
+ *   - Return value 0 (MD_OK) on success, a negative MD_ERR_* code on failure;
+ *     md_last_error() then returns a thread-local message.
+ *   - Host arrays are caller-owned and only read or written during the call; the
+ *     library never keeps a caller pointer. Position, velocity and force arrays are
+ *     N x 3 float64 in C order (x0 y0 z0 x1 y1 z1 ...), particle order = the order of
+ *     the caller's md_set_state.
+ *   - "_dev" variants take device pointers (e.g. a torch tensor's data_ptr) with the
+ *     same layout and a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     the library orders its work after earlier work on that stream and returns
+ *     without synchronising the stream unless stated.
+ *   - A context owns all its device memory; calls on one context must not overlap.
+ *   - Every call reports CUDA failures as MD_ERR_CUDA. Kernels do not trap: they write
+ *     status words (list overflow, non-finite values) that the host checks.
+ */
+#ifndef LJMD_H
+#define LJMD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MD_API __attribute__((visibility("default")))
+#else
+#define MD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_OK 0
+#define MD_ERR_ARG (-1)           /* invalid argument (sizes, box too small, null) */
+#define MD_ERR_OOM (-2)           /* device allocation failed                      */
+#define MD_ERR_LIST_OVERFLOW (-3) /* list capacity could not be grown enough       */
+#define MD_ERR_NONFINITE (-4)     /* a position or velocity became NaN or infinite  */
+#define MD_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                 */
+#define MD_ERR_CUDA (-6)          /* a CUDA runtime call failed                    */
+#define MD_ERR_STATE (-7)         /* call needs a state set by md_set_state first  */
+
+/* Force precision modes (md_set_precision). */
+#define MD_FP64 0       /* all pair arithmetic in FP64                                   */
+#define MD_FP32_FORCE 1 /* pair forces in FP32 from fixed-point separations; positions,  */
+                        /* velocities, list distance tests, energies, virial stay FP64  */
+
+/* Largest particle count of one system (the list packs a slot index in 26 bits). */
+#define MD_MAX_N ((int64_t)((1 << 26) - 1))
+
+typedef struct md_ctx md_ctx;
+
+/* ------------------------------------------------------------ single system */
+
+/* Create a system of N particles in a cubic box of side box_L with cutoff rc and list
+ * skin (Sec. 2.1: the list radius is rc + skin). Requires 0 < N <= MD_MAX_N, rc > 0,
+ * skin >= 0, box_L > 2 (rc + skin) and box_L <= 10000. Precision defaults to MD_FP64.
+ * Allocates all device memory on the current CUDA device; *out receives the handle.
+ * Errors: MD_ERR_ARG, MD_ERR_OOM, MD_ERR_CUDA. */
+MD_API int md_create(double box_L, int64_t N, double rc, double skin, md_ctx** out);
+
+/* Select MD_FP64 or MD_FP32_FORCE. Cached forces are invalidated. */
+MD_API int md_set_precision(md_ctx* ctx, int mode);
+
+/* Copy positions x (N*3, any real values: wrapped into [0, L) on entry) and velocities
+ * v (N*3) from host memory; forces a list rebuild before the next force evaluation. */
+MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v);
+
+/* Same with device pointers (N*3 float64 each), ordered on stream. */
+MD_API int md_set_state_dev(md_ctx* ctx, const double* x_dev, const double* v_dev, void* stream);
+
+/* Copy current positions (wrapped, in [0, L)) and velocities into caller arrays (N*3). */
+MD_API int md_get_state(md_ctx* ctx, double* x, double* v);
+
+/* Same into device arrays (N*3 float64 each), ordered on stream; x or v may be NULL. */
+MD_API int md_get_state_dev(md_ctx* ctx, double* x_dev, double* v_dev, void* stream);
+
+/* Advance nsteps velocity-Verlet steps of size dt (nsteps >= 0). Blocks until done.
+ * Errors: MD_ERR_STATE (no state), MD_ERR_NONFINITE, MD_ERR_LIST_OVERFLOW, MD_ERR_CUDA. */
+MD_API int md_step(md_ctx* ctx, int64_t nsteps, double dt);
+
+/* Same, ordered on the given stream (the call still waits for the per-step list
+ * validity decision, which is read back from the device every step). */
+MD_API int md_step_async(md_ctx* ctx, int64_t nsteps, double dt, void* stream);
+
+/* Forces at the current positions (N*3 host array): F_i = sum_j g(r)(x_j - x_i),
+ * g = 24 r^-8 - 48 r^-14 + 8 c2 for r < rc (Algorithm 1's bracket, Sec. 3.3). */
+MD_API int md_forces(md_ctx* ctx, double* f);
+
+/* Same into a device array (N*3 float64), ordered on stream. */
+MD_API int md_forces_dev(md_ctx* ctx, double* f_dev, void* stream);
+
+/* Observables at the current state (any pointer may be NULL):
+ *   pe     = sum_{i<j} V(r_ij)                        (Eq. 1)
+ *   virial = sum_{i<j} -r_ij V'(r_ij)
+ *   ke     = sum_i |v_i|^2 / 2
+ *   T      = 2 ke / (3 (N - 1))
+ *   P      = (2 ke + virial) / (3 L^3)
+ * Sums are accumulated in FP64 in a fixed order (deterministic). */
+MD_API int md_observables(md_ctx* ctx, double* pe, double* virial, double* ke, double* T, double* P);
+
+/* Counters: list builds since md_create (including forced ones) and steps taken. */
+MD_API int md_stats(md_ctx* ctx, int64_t* rebuilds, int64_t* steps);
+
+/* Build the pair list now at the current positions (normally automatic). */
+MD_API int md_build_list(md_ctx* ctx);
+
+/* Cell of each particle from the last list build, in caller order (N int32):
+ * c = cx + nc (cy + nc cz), c_a = min(floor(x_a nc / L), nc - 1). nc = floor(L / rl),
+ * lowered by one when L / nc < rl (1 + 1e-9), and replaced by 1 when below 3 (every
+ * pair is then a candidate and every cell is 0); nc_out (may be NULL) receives it. */
+MD_API int md_get_cells(md_ctx* ctx, int32_t* cell, int32_t* nc_out);
+
+/* Number of entries of the current full pair list (sum of all list lengths). */
+MD_API int md_list_size(md_ctx* ctx, int64_t* total);
+
+/* Current full list in caller numbering: start[N+1] (int64) and partners[total] (int32)
+ * in the library's internal order per particle (sort to compare as sets). */
+MD_API int md_get_list(md_ctx* ctx, int64_t* start, int32_t* partners);
+
+/* Pair counts of the current list: entries (listed, r < rl at the build) and those
+ * with r < rc at the current positions (FP64 test). */
+MD_API int md_pair_stats(md_ctx* ctx, int64_t* listed, int64_t* within_rc);
+
+/* Device timing of the library's own kernels, taken with CUDA events recorded on
+ * the stream each kernel is launched on. md_set_timing(ctx, 1) enables it and resets
+ * the counters (0 disables). md_get_timing fills out8[8]:
+ *   [0] fused force + integration kernel, total ms   [1] its launches
+ *   [2] pair-list build kernel, total ms              [3] its launches
+ *   [4] binning + sort + gather kernels, total ms     [5] list rebuilds
+ *   [6] kernel launches of all kinds                  [7] 0 (reserved)          */
+MD_API int md_set_timing(md_ctx* ctx, int on);
+MD_API int md_get_timing(md_ctx* ctx, double* out8);
+
+/* Release all resources of ctx (NULL is ignored). */
+MD_API void md_destroy(md_ctx* ctx);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+MD_API const char* md_last_error(void);
+
+/* Library version string. */
+MD_API const char* md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LJMD_H */

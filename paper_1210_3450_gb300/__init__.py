@@ -1,0 +1,7 @@
+"""GB300-native truncated Lennard-Jones molecular dynamics (arXiv:1210.3450 hot path).
+
+The compute path is the CUDA library built from ``csrc/`` (see ``build.py``);
+``ljmd`` is its Python binding.
+"""
+from .ljmd import (LJSystem, MDError, MD_FP32_FORCE, MD_FP64, MD_MAX_N, load_library,  # noqa: F401
+                   version)

@@ -1,0 +1,261 @@
+// C ABI of the LJ-MD library (declared in include/ljmd.h): argument checks and
+// host <-> device marshalling around the engine. Each md_ctx is one system.
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ljmd.h"
+#include "ljmd_engine.h"
+
+struct md_ctx {
+  ljmd::Engine eng;
+  cudaStream_t stream = nullptr;  // library-owned stream for the blocking calls
+};
+
+namespace {
+using ljmd::set_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return MD_ERR_CUDA;
+}
+
+int check_ctx(md_ctx* c) {
+  if (!c) {
+    set_error("null context");
+    return MD_ERR_ARG;
+  }
+  set_error("");
+  return MD_OK;
+}
+
+int64_t n_of(md_ctx* c) { return c->eng.sys(0).spec.n; }
+
+int h2d(md_ctx* c, double* dst, const double* src, int64_t count) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)count, cudaMemcpyHostToDevice, c->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "host to device copy");
+}
+
+int d2h(md_ctx* c, double* dst, const double* src, int64_t count) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+  e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "stream synchronize");
+}
+}  // namespace
+
+extern "C" {
+
+int md_create(double box_L, int64_t N, double rc, double skin, md_ctx** out) {
+  set_error("");
+  if (!out) {
+    set_error("null output handle");
+    return MD_ERR_ARG;
+  }
+  *out = nullptr;
+  md_ctx* c = new (std::nothrow) md_ctx();
+  if (!c) {
+    set_error("host allocation failed");
+    return MD_ERR_OOM;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  std::vector<ljmd::SysSpec> specs{{N, box_L, rc, skin}};
+  int r = c->eng.init(specs, MD_FP64);
+  if (r != MD_OK) {
+    std::string msg = ljmd::last_error_cstr();
+    cudaStreamDestroy(c->stream);
+    delete c;
+    set_error(msg);
+    return r;
+  }
+  *out = c;
+  return MD_OK;
+}
+
+int md_set_precision(md_ctx* c, int mode) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.set_precision(mode);
+}
+
+int md_set_state(md_ctx* c, const double* x, const double* v) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!x || !v) {
+    set_error("null state array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = n_of(c);
+  double* st = c->eng.stage();
+  if ((r = h2d(c, st, x, 3 * n))) return r;
+  if ((r = h2d(c, st + 3 * n, v, 3 * n))) return r;
+  if ((r = c->eng.set_state_dev(0, st, st + 3 * n, c->stream))) return r;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "stream synchronize");
+}
+
+int md_set_state_dev(md_ctx* c, const double* x, const double* v, void* stream) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!x || !v) {
+    set_error("null state array");
+    return MD_ERR_ARG;
+  }
+  return c->eng.set_state_dev(0, x, v, (cudaStream_t)stream);
+}
+
+int md_get_state(md_ctx* c, double* x, double* v) {
+  int r = check_ctx(c);
+  if (r) return r;
+  const int64_t n = n_of(c);
+  double* st = c->eng.stage();
+  if ((r = c->eng.get_state_dev(0, x ? st : nullptr, v ? st + 3 * n : nullptr, c->stream))) return r;
+  if (x && (r = d2h(c, x, st, 3 * n))) return r;
+  if (v && (r = d2h(c, v, st + 3 * n, 3 * n))) return r;
+  return MD_OK;
+}
+
+int md_get_state_dev(md_ctx* c, double* x, double* v, void* stream) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.get_state_dev(0, x, v, (cudaStream_t)stream);
+}
+
+int md_step_async(md_ctx* c, int64_t nsteps, double dt, void* stream) {
+  int r = check_ctx(c);
+  if (r) return r;
+  std::vector<double> dts{dt};
+  return c->eng.step(nsteps, dts, (cudaStream_t)stream);
+}
+
+int md_step(md_ctx* c, int64_t nsteps, double dt) {
+  int r = check_ctx(c);
+  if (r) return r;
+  std::vector<double> dts{dt};
+  return c->eng.step(nsteps, dts, c->stream);
+}
+
+int md_forces(md_ctx* c, double* f) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!f) {
+    set_error("null force array");
+    return MD_ERR_ARG;
+  }
+  double* st = c->eng.stage();
+  if ((r = c->eng.forces_dev(0, st, c->stream))) return r;
+  return d2h(c, f, st, 3 * n_of(c));
+}
+
+int md_forces_dev(md_ctx* c, double* f, void* stream) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!f) {
+    set_error("null force array");
+    return MD_ERR_ARG;
+  }
+  return c->eng.forces_dev(0, f, (cudaStream_t)stream);
+}
+
+int md_observables(md_ctx* c, double* pe, double* virial, double* ke, double* T, double* P) {
+  int r = check_ctx(c);
+  if (r) return r;
+  double o[3];
+  if ((r = c->eng.observables(o, c->stream))) return r;
+  const int64_t n = n_of(c);
+  const double L = c->eng.sys(0).spec.L;
+  if (pe) *pe = o[0];
+  if (virial) *virial = o[1];
+  if (ke) *ke = o[2];
+  if (T) *T = n > 1 ? 2.0 * o[2] / (3.0 * (double)(n - 1)) : 0.0;
+  if (P) *P = (2.0 * o[2] + o[1]) / (3.0 * L * L * L);
+  return MD_OK;
+}
+
+int md_stats(md_ctx* c, int64_t* rebuilds, int64_t* steps) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (rebuilds) *rebuilds = c->eng.sys(0).rebuilds;
+  if (steps) *steps = c->eng.sys(0).steps;
+  return MD_OK;
+}
+
+int md_build_list(md_ctx* c) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.build_lists(c->stream);
+}
+
+int md_get_cells(md_ctx* c, int32_t* cell, int32_t* nc_out) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (nc_out) *nc_out = c->eng.sys(0).nc;
+  if (!cell) return MD_OK;
+  return c->eng.get_cells(0, cell, c->stream);
+}
+
+int md_list_size(md_ctx* c, int64_t* total) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!total) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  return c->eng.list_size(0, total, c->stream);
+}
+
+int md_get_list(md_ctx* c, int64_t* start, int32_t* partners) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!start || !partners) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  return c->eng.get_list(0, start, partners, c->stream);
+}
+
+int md_set_timing(md_ctx* c, int on) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.set_timing(on != 0);
+}
+
+int md_get_timing(md_ctx* c, double* out8) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!out8) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  c->eng.get_timing(out8);
+  return MD_OK;
+}
+
+int md_pair_stats(md_ctx* c, int64_t* listed, int64_t* within_rc) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!listed || !within_rc) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  return c->eng.pair_stats(0, listed, within_rc, c->stream);
+}
+
+void md_destroy(md_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaStream_t s = c->stream;
+  delete c;
+  if (s) cudaStreamDestroy(s);
+}
+
+const char* md_last_error(void) { return ljmd::last_error_cstr(); }
+
+const char* md_version(void) { return "ljmd 0.1 (sm_103a)"; }
+
+}  // extern "C"

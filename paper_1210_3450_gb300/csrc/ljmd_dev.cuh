@@ -1,0 +1,117 @@
+// Device-side data layout and kernel declarations of the LJ-MD engine.
+//
+// Every system lives in a contiguous, 32-aligned range of "slots" of the shared
+// particle arrays. Between list builds the particles of a system are stored in
+// cell order (Sec. 2.1 grid method; positions sorted by cell give coalesced
+// neighbour loads). A warp owns one tile of 32 consecutive slots of one system.
+//
+// Pair list (Sec. 2.1 "sorted pair list", Fig. 1) in a transposed key-pointer form:
+// the partners of the particle in lane l of tile t are entries
+//     nbr[list_off + (t_local * kmax + k) * 32 + l],  k < ncnt[slot],
+// so one warp reads 32 consecutive words per k. An entry packs the partner's
+// slot index relative to the system (bits 0..25) and the periodic image of the
+// partner (bits 26..31: two bits per axis, 0 = same image, 1 = +L, 2 = -L).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ljmd {
+
+constexpr int kTile = 32;
+constexpr int kIdxBits = 26;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+
+// Per-system constants (device copy), written by the host.
+struct SysParams {
+  double L;          // box side
+  double invL;       // 1 / L
+  double inv_cs;     // nc / L (cells per unit length)
+  double rc2;        // rc^2
+  double rl2;        // (rc + skin)^2
+  double c2, c0;     // Eq. 1 coefficients
+  double dt;         // time step of the current md_step call
+  double qscale;     // 2^32 / L: fixed-point scale of the shadow positions
+  float qunit;       // L / 2^32 as float: fixed-point unit
+  float rl2q_lo;     // rl^2 (1 - 1e-5) in fixed-point units^2: certainly inside below
+  float rl2q_hi;     // rl^2 (1 + 1e-5) in fixed-point units^2: certainly outside above
+  float rc2f;        // rc^2 as float (FP32 force cutoff)
+  float c2f;         // c2 as float
+  int64_t p_off;     // first slot
+  int64_t c_off;     // first cell (cell arrays hold ncell + 1 entries per system)
+  int64_t l_off;     // first list word
+  int32_t n;         // particles
+  int32_t nc;        // cells per axis; 1 = every pair is a candidate
+  int32_t kmax;      // list capacity per particle
+  int32_t t_off;     // first global tile
+  int32_t ntiles;    // tiles of this system
+  int32_t active;    // 1 if the system takes part in the current launches
+  int32_t pad_;
+};
+
+// Per-system status words written by kernels and read by the host.
+struct SysStatus {
+  int32_t overflow;   // largest list length that did not fit (0 = none)
+  int32_t nonfinite;  // 1 if a position or velocity became non-finite
+  int32_t max_count;  // largest list length of the last build
+  int32_t pad_;
+};
+
+// Kernel flags of the fused force + integration step.
+enum StepFlags : int {
+  kStepDrift = 1,       // drift x by dt v after the kicks (writes the other x buffer)
+  kStepStoreF = 2,      // store F (double) for md_forces / the next call
+  kStepUseStoredF = 4,  // take F from the stored buffer instead of the pair loop
+};
+
+struct DevArrays {
+  double4_32a* x[2];      // positions (w unused), ping-pong by step parity
+  double4_32a* v;         // velocities
+  double4_32a* xref;      // positions at the last list build
+  double4_32a* f;         // stored forces (double)
+  int4* xq[2];        // fixed-point shadow positions (uint32 per axis, wraps at L)
+  int32_t* id;        // caller index of each slot, -1 for padding
+  int32_t* cell;      // cell of each slot (valid after binning)
+  int32_t* ncnt;      // list length of each slot
+  uint32_t* nbr;      // list words
+  double* tile_obs;   // per-tile (PE, W, KE) partial sums for observables
+  // rebuild scratch
+  double4_32a* xtmp;
+  double4_32a* vtmp;
+  int32_t* idtmp;
+  int32_t* celltmp;
+  int32_t* perm;      // new slot -> old slot
+  int32_t* ccount;    // particles per cell (then fill counters)
+  int32_t* cstart;    // first slot of each cell (relative to the system), ncell + 1 per system
+  // systems
+  const SysParams* params;
+  SysStatus* status;
+  unsigned long long* disp2;  // per system: max squared displacement (double bits)
+  const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
+  const int32_t* tile_sys;  // system of each global tile
+  int32_t ntiles;
+};
+
+// ---------------------------------------------------------------- launchers
+// All launches cover every tile of every active system; warps of inactive
+// systems (or of systems not rebuilding, for the rebuild kernels) return early.
+
+void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
+void launch_cell_scan(const DevArrays& a, int nsys, cudaStream_t s);
+void launch_scatter(const DevArrays& a, cudaStream_t s);
+void launch_cell_sort(const DevArrays& a, int nsys, int64_t max_cells, cudaStream_t s);
+void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
+void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
+void launch_build_list(const DevArrays& a, int cur, cudaStream_t s);
+void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags,
+                      cudaStream_t s);
+void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags,
+                      cudaStream_t s);
+void launch_pe_virial(const DevArrays& a, int cur, cudaStream_t s);
+void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s);
+void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, cudaStream_t s);
+void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n,
+                      int sys, int64_t ntiles_sys, cudaStream_t s);
+void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v,
+                        int sys, int64_t ntiles_sys, cudaStream_t s);
+
+}  // namespace ljmd

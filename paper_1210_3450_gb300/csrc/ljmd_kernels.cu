@@ -1,0 +1,677 @@
+// CUDA kernels of the LJ-MD hot path for sm_103a.
+//
+// Paper: Watanabe, Suzuki, Ito, "Huge-scale Molecular Dynamics Simulation of
+// Multibubble Nuclei" (arXiv:1210.3450).
+//   cell binning (counting sort)          - Sec. 2.1 grid / linked-list method
+//   pair-list build with skin             - Sec. 2.1 bookkeeping method, Fig. 1
+//   force loop (full list, no 3rd law)    - Sec. 3.3, Algorithm 1, Eq. 1
+//   velocity-Verlet update, periodic box  - Sec. 3.2 / 4.1 (second-order symplectic)
+//   displacement-triggered list check     - Sec. 2.1 (list validity every step)
+//   PE / virial / KE reductions           - Sec. 2.2, 4.3 (energy and pressure)
+//
+// Work layout: one warp per tile of 32 consecutive slots of one system, one
+// thread per particle ("key" particle data stays in registers, Sec. 2.1); the
+// partner loop reads the transposed list so each k is one coalesced 128-byte load.
+//
+// Decisions that must agree bit for bit with a plain FP64 reference (cell of a
+// particle, list membership, wrap into the box, displacement) use explicitly
+// rounded FP64 intrinsics (__dadd_rn, __dmul_rn, ...), so the compiler cannot fuse
+// them into FMAs.
+#include "ljmd_dev.cuh"
+
+namespace ljmd {
+
+namespace {
+
+constexpr int kBlock = 128;  // 4 tiles per block
+constexpr unsigned kFull = 0xffffffffu;
+
+struct TileCtx {
+  int sys;
+  int tl;       // tile index within the system
+  int local;    // slot index within the system
+  int64_t s;    // global slot
+  bool act;     // lane holds a particle
+};
+
+// Returns false if the whole warp has nothing to do.
+__device__ __forceinline__ bool tile_ctx(const DevArrays& a, TileCtx& t, SysParams& P) {
+  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.ntiles) return false;
+  t.sys = a.tile_sys[warp];
+  P = a.params[t.sys];
+  if (!P.active) return false;
+  t.tl = warp - P.t_off;
+  t.local = t.tl * kTile + lane;
+  t.s = P.p_off + t.local;
+  t.act = t.local < P.n;
+  return true;
+}
+
+// x - L floor(x / L), then the same fix-ups as the reference wrap.
+__device__ __forceinline__ double wrap_full(double x, double L) {
+  double w = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+  if (w < 0.0) w = __dadd_rn(w, L);
+  if (w >= L) w = __dsub_rn(w, L);
+  if (w < 0.0 || w >= L) w = 0.0;
+  return w;
+}
+
+// Wrap only when outside [0, L): for x >= 0 the bit pattern orders like the value,
+// and negative values (sign bit set) or NaN compare above L's bit pattern.
+__device__ __forceinline__ double wrap_fast(double x, double L) {
+  if ((unsigned long long)__double_as_longlong(x) >= (unsigned long long)__double_as_longlong(L))
+    x = wrap_full(x, L);
+  return x;
+}
+
+__device__ __forceinline__ int cell_axis(double x, double inv_cs, int nc) {
+  int k = (int)floor(__dmul_rn(x, inv_cs));
+  if (k > nc - 1) k = nc - 1;
+  if (k < 0) k = 0;
+  return k;
+}
+
+__device__ __forceinline__ int cell_of(const double4_32a& x, double inv_cs, int nc) {
+  return cell_axis(x.x, inv_cs, nc) + nc * (cell_axis(x.y, inv_cs, nc) + nc * cell_axis(x.z, inv_cs, nc));
+}
+
+// Fixed-point shadow coordinate: round(x 2^32 / L) mod 2^32. Differences of two
+// such values, taken as wrapped 32-bit integers, are minimum-image separations.
+__device__ __forceinline__ int to_fixed(double x, double qscale) {
+  return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
+}
+
+__device__ __forceinline__ int4 fixed4(const double4_32a& x, double qscale) {
+  return make_int4(to_fixed(x.x, qscale), to_fixed(x.y, qscale), to_fixed(x.z, qscale), 0);
+}
+
+__device__ __forceinline__ int wrapped_diff(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
+
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// Apply the periodic image encoded in a list word (two bits per axis).
+__device__ __forceinline__ double apply_image(double d, unsigned code2, double L) {
+  if (code2 == 1u) return __dadd_rn(d, L);
+  if (code2 == 2u) return __dsub_rn(d, L);
+  return d;
+}
+
+// 1 / r2 in FP64 without the FP64 divide sequence: a float seed built from the
+// top mantissa bits by integer operations, a hardware reciprocal estimate, and one
+// cubically convergent correction y = y0 (1 + e + e^2), e = 1 - r2 y0. The seed's
+// relative error is below 2^-21, so the result is within rounding of 1 / r2.
+// Valid for 1e-37 < r2 < 1e37.
+__device__ __forceinline__ double rcp_f64(double r2) {
+  const long long b = __double_as_longlong(r2);
+  const int hi = (int)(b >> 32);
+  const unsigned lo = (unsigned)b;
+  const int fb = (((hi >> 20) - 896) << 23) | ((hi & 0xFFFFF) << 3) | (int)(lo >> 29);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float(fb)));
+  const int yb = __float_as_int(yf);
+  const long long db = ((long long)((((yb >> 23) + 896) << 20) | ((yb & 0x7FFFFF) >> 3)) << 32) |
+                       ((long long)(yb & 7) << 29);
+  const double y0 = __longlong_as_double(db);
+  const double e = fma(-r2, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host <-> slots
+
+__global__ void k_from_caller(DevArrays a, int cur, const double* __restrict__ x,
+                              const double* __restrict__ v, int sys) {
+  const SysParams P = a.params[sys];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= (int64_t)P.ntiles * kTile) return;
+  const int64_t s = P.p_off + l;
+  if (l < P.n) {
+    a.x[cur][s] = make_double4_32a(wrap_full(x[3 * l + 0], P.L), wrap_full(x[3 * l + 1], P.L),
+                               wrap_full(x[3 * l + 2], P.L), 0.0);
+    a.v[s] = make_double4_32a(v[3 * l + 0], v[3 * l + 1], v[3 * l + 2], 0.0);
+    a.id[s] = (int32_t)l;
+  } else {
+    a.x[cur][s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    a.v[s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    a.id[s] = -1;
+    a.ncnt[s] = 0;
+  }
+}
+
+// which: 0 = positions, 1 = velocities, 2 = stored forces, 3 = cells (as double)
+__global__ void k_to_caller(DevArrays a, int cur, int which, double* __restrict__ out, int sys) {
+  const SysParams P = a.params[sys];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= P.n) return;
+  const int64_t s = P.p_off + l;
+  const int64_t i = a.id[s];
+  double4_32a q;
+  if (which == 0) {
+    q = a.x[cur][s];  // positions drift outside [0, L) between list builds
+    q.x = wrap_fast(q.x, P.L);
+    q.y = wrap_fast(q.y, P.L);
+    q.z = wrap_fast(q.z, P.L);
+  } else if (which == 1) {
+    q = a.v[s];
+  } else {
+    q = a.f[s];
+  }
+  out[3 * i + 0] = q.x;
+  out[3 * i + 1] = q.y;
+  out[3 * i + 2] = q.z;
+}
+
+// --------------------------------------------------------- binning (Sec. 2.1)
+
+__global__ void k_cell_count(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  // Positions are wrapped into [0, L) only here (at a list build): between
+  // builds they move freely so that the periodic images stored in the list
+  // stay valid.
+  double4_32a x = a.x[cur][t.s];
+  const double4_32a w = make_double4_32a(wrap_fast(x.x, P.L), wrap_fast(x.y, P.L), wrap_fast(x.z, P.L), 0.0);
+  if (w.x != x.x || w.y != x.y || w.z != x.z) a.x[cur][t.s] = w;
+  int c = 0;
+  if (P.nc > 1) {
+    c = cell_of(w, P.inv_cs, P.nc);
+    atomicAdd(&a.ccount[P.c_off + c], 1);
+  }
+  a.cell[t.s] = c;
+}
+
+// Exclusive scan of the cell counts of one system per block; the counts are
+// then reset to serve as fill counters of the scatter.
+__global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nsys) {
+  const int sys = blockIdx.x;
+  if (sys >= nsys) return;
+  const SysParams P = a.params[sys];
+  if (!P.active || !a.rebuild[sys]) return;
+  __shared__ int wsum[32];
+  __shared__ int total_s;
+  const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int carry = 0;
+  for (int64_t base = 0; base < ncell; base += 1024) {
+    const int64_t c = base + tid;
+    const int val = c < ncell ? a.ccount[P.c_off + c] : 0;
+    int incl = val;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int ws = wsum[lane];
+      int wi = ws;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - ws;
+      if (lane == 31) total_s = wi;
+    }
+    __syncthreads();
+    if (c < ncell) {
+      a.cstart[P.c_off + c] = carry + wsum[w] + incl - val;
+      a.ccount[P.c_off + c] = 0;
+    }
+    carry += total_s;
+    __syncthreads();
+  }
+  if (tid == 0) a.cstart[P.c_off + ncell] = carry;
+}
+
+__global__ void k_scatter(DevArrays a) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  if (P.nc == 1) {
+    a.perm[t.s] = t.local;
+    return;
+  }
+  const int c = a.cell[t.s];
+  const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
+  a.perm[P.p_off + pos] = t.local;
+}
+
+// Order the particles of each cell by caller index (makes the scatter stable
+// and the whole build deterministic). Insertion sort: cells hold tens of particles.
+__global__ void k_cell_sort(DevArrays a) {
+  const int sys = blockIdx.y;
+  const SysParams P = a.params[sys];
+  if (!P.active || !a.rebuild[sys] || P.nc == 1) return;
+  const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
+  a.ccount[P.c_off + c] = 0;  // ready for the next binning
+  int32_t* pm = a.perm + P.p_off;
+  const int32_t* id = a.id + P.p_off;
+  for (int k = lo + 1; k < hi; ++k) {
+    const int32_t pk = pm[k];
+    const int32_t key = id[pk];
+    int m = k - 1;
+    while (m >= lo && id[pm[m]] > key) {
+      pm[m + 1] = pm[m];
+      --m;
+    }
+    pm[m + 1] = pk;
+  }
+}
+
+__global__ void k_gather(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  const int64_t old = P.p_off + a.perm[t.s];
+  a.xtmp[t.s] = a.x[cur][old];
+  a.vtmp[t.s] = a.v[old];
+  a.idtmp[t.s] = a.id[old];
+  a.celltmp[t.s] = a.cell[old];
+}
+
+__global__ void k_copyback(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  const double4_32a x = a.xtmp[t.s];
+  a.x[cur][t.s] = x;
+  a.xref[t.s] = x;
+  a.xq[cur][t.s] = fixed4(x, P.qscale);
+  a.v[t.s] = a.vtmp[t.s];
+  a.id[t.s] = a.idtmp[t.s];
+  a.cell[t.s] = a.celltmp[t.s];
+}
+
+// ----------------------------------------------- pair list (Sec. 2.1, Fig. 1)
+
+// Full list: every j != i with minimum-image r^2 < rl^2 (strict). Candidates
+// come from the 27 neighbour cells (or all particles when nc == 1). The decision
+// is the FP64 test ((dx dx + dy dy) + dz dz < rl^2, no fused operations). It is
+// taken first from the fixed-point separation in FP32, whose relative error on
+// r^2 is below 3.2e-6 for L <= 10^4 (quantisation <= 1 unit per axis, at least
+// 1.2e6 units per rl; five FP32 roundings): below rl^2 (1 - 1e-5) the pair is
+// certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only the thin
+// shell between needs the FP64 test. The result is identical to always taking it.
+__global__ void __launch_bounds__(kBlock) k_build_list(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  const int lane = threadIdx.x & 31;
+  const double4_32a xi = a.x[cur][t.s];
+  const int4 qi = a.xq[cur][t.s];
+  const double4_32a* xs = a.x[cur] + P.p_off;
+  const int4* qs = a.xq[cur] + P.p_off;
+  uint32_t* out = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+  const int kmax = P.kmax;
+  int count = 0;
+
+  auto test = [&](int j, unsigned code) {
+    const int4 qj = qs[j];
+    const float ax = (float)wrapped_diff(qj.x, qi.x);
+    const float ay = (float)wrapped_diff(qj.y, qi.y);
+    const float az = (float)wrapped_diff(qj.z, qi.z);
+    const float r2q = ax * ax + ay * ay + az * az;
+    if (!(r2q < P.rl2q_hi)) return;
+    bool inside = r2q < P.rl2q_lo;
+    if (!inside) {
+      const double4_32a xj = xs[j];
+      const double dx = apply_image(__dsub_rn(xj.x, xi.x), code & 3u, P.L);
+      const double dy = apply_image(__dsub_rn(xj.y, xi.y), (code >> 2) & 3u, P.L);
+      const double dz = apply_image(__dsub_rn(xj.z, xi.z), (code >> 4) & 3u, P.L);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      inside = r2 < P.rl2;
+    }
+    if (inside) {
+      if (count < kmax) out[(int64_t)count * kTile] = (uint32_t)j | (code << kIdxBits);
+      ++count;
+    }
+  };
+
+  if (P.nc > 1) {
+    const int nc = P.nc;
+    const int ci = a.cell[t.s];
+    const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
+    const int32_t* cst = a.cstart + P.c_off;
+    for (int oz = -1; oz <= 1; ++oz) {
+      int nz = cz + oz;
+      unsigned shz = 0;
+      if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
+      for (int oy = -1; oy <= 1; ++oy) {
+        int ny = cy + oy;
+        unsigned shy = 0;
+        if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
+        for (int ox = -1; ox <= 1; ++ox) {
+          int nx = cx + ox;
+          unsigned shx = 0;
+          if (nx < 0) { nx += nc; shx = 2; } else if (nx >= nc) { nx -= nc; shx = 1; }
+          const int c = nx + nc * (ny + nc * nz);
+          const unsigned code = shx | (shy << 2) | (shz << 4);
+          const int lo = cst[c], hi = cst[c + 1];
+          for (int j = lo; j < hi; ++j)
+            if (j != t.local) test(j, code);
+        }
+      }
+    }
+  } else {
+    // every other particle; the image is the minimum image of the FP64 separation
+    for (int j = 0; j < P.n; ++j) {
+      if (j == t.local) continue;
+      const double4_32a xj = xs[j];
+      unsigned code = 0;
+      const double d[3] = {__dsub_rn(xj.x, xi.x), __dsub_rn(xj.y, xi.y), __dsub_rn(xj.z, xi.z)};
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const double k = rint(__ddiv_rn(d[ax], P.L));
+        if (k > 0.5) code |= 2u << (2 * ax);
+        else if (k < -0.5) code |= 1u << (2 * ax);
+      }
+      test(j, code);
+    }
+  }
+  a.ncnt[t.s] = count < kmax ? count : kmax;
+  if (count > kmax) atomicMax(&a.status[t.sys].overflow, count);
+  atomicMax(&a.status[t.sys].max_count, count);
+}
+
+// ------------------------------------- fused force + velocity-Verlet step
+
+// One launch: F at x[cur] from the list (or the stored F), then
+//   v += ka dt F   (completes the previous step),
+//   v += kb dt F   (first half-kick of the next step),
+//   x' = wrap(x + dt v) into x[cur ^ 1] (flags & kStepDrift),
+// and the largest squared displacement since the list build into disp2[sys].
+template <bool kFP32>
+__global__ void __launch_bounds__(kBlock) k_step(DevArrays a, int cur, double ka, double kb, int flags) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P)) return;
+  const int lane = threadIdx.x & 31;
+  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+  if (t.act) xi = a.x[cur][t.s];
+  if (flags & kStepUseStoredF) {
+    if (t.act) {
+      const double4_32a f = a.f[t.s];
+      Fx = f.x; Fy = f.y; Fz = f.z;
+    }
+  } else if (t.act) {
+    const int cnt = a.ncnt[t.s];
+    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+    if (kFP32) {
+      // Pair arithmetic in FP32 from exact fixed-point separations (the integer
+      // difference of the shadow coordinates is already the minimum image).
+      const int4* qs = a.xq[cur] + P.p_off;
+      const int4 qi = a.xq[cur][t.s];
+      const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
+      float fx = 0.f, fy = 0.f, fz = 0.f;
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t e = __ldg(lp + (int64_t)k * kTile);
+        const int4 qj = qs[e & kIdxMask];
+        const float dx = (float)wrapped_diff(qj.x, qi.x) * qu;
+        const float dy = (float)wrapped_diff(qj.y, qi.y) * qu;
+        const float dz = (float)wrapped_diff(qj.z, qi.z) * qu;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+          const float ir2 = __frcp_rn(r2);
+          const float ir6 = ir2 * ir2 * ir2;
+          const float g = ir2 * ir6 * (24.0f - 48.0f * ir6) + c2x8;
+          fx = fmaf(g, dx, fx);
+          fy = fmaf(g, dy, fy);
+          fz = fmaf(g, dz, fz);
+        }
+      }
+      Fx = fx; Fy = fy; Fz = fz;
+    } else {
+      const double4_32a* xs = a.x[cur] + P.p_off;
+      const long long rc2b = __double_as_longlong(P.rc2);
+      const double c2x8 = 8.0 * P.c2, L = P.L;
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t e = __ldg(lp + (int64_t)k * kTile);
+        const double4_32a xj = xs[e & kIdxMask];
+        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const unsigned code = e >> kIdxBits;
+        if (code) {
+          dx = apply_image(dx, code & 3u, L);
+          dy = apply_image(dy, (code >> 2) & 3u, L);
+          dz = apply_image(dz, (code >> 4) & 3u, L);
+        }
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (__double_as_longlong(r2) < rc2b) {  // r2 >= 0: integer order = value order
+          const double ir2 = rcp_f64(r2);
+          const double ir4 = ir2 * ir2;
+          const double ir6 = ir4 * ir2;
+          const double ir8 = ir4 * ir4;
+          const double g = fma(ir8, fma(-48.0, ir6, 24.0), c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+          Fx = fma(g, dx, Fx);
+          Fy = fma(g, dy, Fy);
+          Fz = fma(g, dz, Fz);
+        }
+      }
+    }
+  }
+  unsigned long long d2b = 0ull;
+  if (t.act) {
+    if (flags & kStepStoreF) a.f[t.s] = make_double4_32a(Fx, Fy, Fz, 0.0);
+    double4_32a v = a.v[t.s];
+    const double dt = P.dt;
+    if (ka != 0.0) {
+      const double h = ka * dt;
+      v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z);
+    }
+    if (kb != 0.0) {
+      const double h = kb * dt;
+      v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z);
+    }
+    a.v[t.s] = v;
+    if (flags & kStepDrift) {
+      // no wrap here: images in the list assume unwrapped motion since the build
+      double4_32a xn;
+      xn.x = fma(dt, v.x, xi.x);
+      xn.y = fma(dt, v.y, xi.y);
+      xn.z = fma(dt, v.z, xi.z);
+      xn.w = 0.0;
+      a.x[cur ^ 1][t.s] = xn;
+      if (kFP32) a.xq[cur ^ 1][t.s] = fixed4(xn, P.qscale);
+      if (!(finite_bits(xn.x) && finite_bits(xn.y) && finite_bits(xn.z) && finite_bits(v.x) &&
+            finite_bits(v.y) && finite_bits(v.z)))
+        a.status[t.sys].nonfinite = 1;
+      // displacement since the list build (positions are not wrapped in between)
+      const double4_32a r = a.xref[t.s];
+      const double ex = __dsub_rn(xn.x, r.x);
+      const double ey = __dsub_rn(xn.y, r.y);
+      const double ez = __dsub_rn(xn.z, r.z);
+      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+      d2b = (unsigned long long)__double_as_longlong(d2);
+      if (!finite_bits(d2)) d2b = 0x7ff0000000000000ull;
+    }
+  }
+  if (flags & kStepDrift) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(kFull, d2b, o);
+      d2b = y > d2b ? y : d2b;
+    }
+    if (lane == 0 && d2b) atomicMax(&a.disp2[t.sys], d2b);
+  }
+}
+
+// ------------------------------------------------- observables (FP64 sums)
+
+// Per particle: 1/2 sum_j V(r) and 1/2 sum_j -r V'(r) over listed partners with
+// r < rc (the full list counts each pair twice), and 1/2 |v|^2; each tile sums
+// its 32 values in a fixed shuffle order into tile_obs[3 t ...].
+__global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P)) return;
+  const int lane = threadIdx.x & 31;
+  double pe = 0.0, w = 0.0, ke = 0.0;
+  if (t.act) {
+    const double4_32a xi = a.x[cur][t.s];
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    const int cnt = a.ncnt[t.s];
+    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t e = lp[(int64_t)k * kTile];
+      const double4_32a xj = xs[e & kIdxMask];
+      const unsigned code = e >> kIdxBits;
+      const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
+      const double dy = apply_image(xj.y - xi.y, (code >> 2) & 3u, P.L);
+      const double dz = apply_image(xj.z - xi.z, (code >> 4) & 3u, P.L);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < P.rc2) {
+        const double ir2 = 1.0 / r2;
+        const double ir6 = ir2 * ir2 * ir2;
+        pe += 4.0 * (ir6 * ir6 - ir6 + P.c2 * r2 + P.c0);
+        w += 48.0 * ir6 * ir6 - 24.0 * ir6 - 8.0 * P.c2 * r2;
+      }
+    }
+    pe *= 0.5;
+    w *= 0.5;
+    const double4_32a v = a.v[t.s];
+    ke = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pe += __shfl_xor_sync(kFull, pe, o);
+    w += __shfl_xor_sync(kFull, w, o);
+    ke += __shfl_xor_sync(kFull, ke, o);
+  }
+  if (lane == 0) {
+    const int64_t g = (int64_t)(P.t_off + t.tl) * 3;
+    a.tile_obs[g + 0] = pe;
+    a.tile_obs[g + 1] = w;
+    a.tile_obs[g + 2] = ke;
+  }
+}
+
+// Counts of listed pairs and of listed pairs with r < rc (FP64 test), per system.
+__global__ void __launch_bounds__(kBlock) k_pair_stats(DevArrays a, int cur, unsigned long long* out2) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P)) return;
+  const int lane = threadIdx.x & 31;
+  unsigned listed = 0, inside = 0;
+  if (t.act) {
+    const double4_32a xi = a.x[cur][t.s];
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    const int cnt = a.ncnt[t.s];
+    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+    listed = (unsigned)cnt;
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t e = lp[(int64_t)k * kTile];
+      const double4_32a xj = xs[e & kIdxMask];
+      const unsigned code = e >> kIdxBits;
+      const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
+      const double dy = apply_image(xj.y - xi.y, (code >> 2) & 3u, P.L);
+      const double dz = apply_image(xj.z - xi.z, (code >> 4) & 3u, P.L);
+      if (dx * dx + dy * dy + dz * dz < P.rc2) ++inside;
+    }
+  }
+  listed = __reduce_add_sync(kFull, listed);
+  inside = __reduce_add_sync(kFull, inside);
+  if (lane == 0) {
+    atomicAdd(&out2[2 * t.sys + 0], (unsigned long long)listed);
+    atomicAdd(&out2[2 * t.sys + 1], (unsigned long long)inside);
+  }
+}
+
+// One block per system: fixed-order sum of its tile partials (deterministic).
+__global__ void __launch_bounds__(256) k_reduce_obs(DevArrays a, int nsys, double* out3) {
+  const int sys = blockIdx.x;
+  if (sys >= nsys) return;
+  const SysParams P = a.params[sys];
+  if (!P.active) return;
+  __shared__ double sh[3][256];
+  double pe = 0.0, w = 0.0, ke = 0.0;
+  for (int q = threadIdx.x; q < P.ntiles; q += blockDim.x) {
+    const double* o = a.tile_obs + (int64_t)(P.t_off + q) * 3;
+    pe += o[0];
+    w += o[1];
+    ke += o[2];
+  }
+  sh[0][threadIdx.x] = pe;
+  sh[1][threadIdx.x] = w;
+  sh[2][threadIdx.x] = ke;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out3[3 * sys + 0] = sh[0][0];
+    out3[3 * sys + 1] = sh[1][0];
+    out3[3 * sys + 2] = sh[2][0];
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+namespace {
+inline unsigned tile_blocks(const DevArrays& a) {
+  return (unsigned)(((int64_t)a.ntiles * kTile + kBlock - 1) / kBlock);
+}
+}  // namespace
+
+void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v, int sys,
+                        int64_t ntiles_sys, cudaStream_t s) {
+  const int64_t n = ntiles_sys * kTile;
+  k_from_caller<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, cur, x, v, sys);
+}
+
+void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n, int sys,
+                      int64_t, cudaStream_t s) {
+  if (sys_n <= 0) return;
+  k_to_caller<<<(unsigned)((sys_n + 255) / 256), 256, 0, s>>>(a, cur, which, out, sys);
+}
+
+void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
+  k_cell_count<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+}
+void launch_cell_scan(const DevArrays& a, int nsys, cudaStream_t s) {
+  k_cell_scan<<<nsys, 1024, 0, s>>>(a, nsys);
+}
+void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<tile_blocks(a), kBlock, 0, s>>>(a); }
+void launch_cell_sort(const DevArrays& a, int nsys, int64_t max_cells, cudaStream_t s) {
+  dim3 g((unsigned)((max_cells + 127) / 128), (unsigned)nsys);
+  k_cell_sort<<<g, 128, 0, s>>>(a);
+}
+void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<tile_blocks(a), kBlock, 0, s>>>(a, cur); }
+void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
+  k_copyback<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+}
+void launch_build_list(const DevArrays& a, int cur, cudaStream_t s) {
+  k_build_list<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+}
+void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
+  k_step<false><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+}
+void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
+  k_step<true><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+}
+void launch_pe_virial(const DevArrays& a, int cur, cudaStream_t s) {
+  k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+}
+void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s) {
+  k_pair_stats<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, out2);
+}
+void launch_reduce_obs(const DevArrays& a, int, int nsys, double* out3, cudaStream_t s) {
+  k_reduce_obs<<<nsys, 256, 0, s>>>(a, nsys, out3);
+}
+
+}  // namespace ljmd

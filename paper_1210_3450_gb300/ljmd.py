@@ -1,0 +1,239 @@
+"""Python binding of the C ABI in ``include/ljmd.h`` (ctypes; argument
+marshalling only). Every computation runs in the CUDA library
+``_build/libljmd.so``; there is no CPU fallback: loading fails loudly if the
+library is missing or cannot be loaded.
+
+Host-array calls take numpy arrays of shape (N, 3), float64. The ``*_dev``
+calls take CUDA torch tensors (float64, contiguous) and an optional
+``torch.cuda.Stream``; torch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+MD_OK = 0
+MD_ERR_ARG = -1
+MD_ERR_OOM = -2
+MD_ERR_LIST_OVERFLOW = -3
+MD_ERR_NONFINITE = -4
+MD_ERR_TIMEOUT = -5
+MD_ERR_CUDA = -6
+MD_ERR_STATE = -7
+MD_FP64 = 0
+MD_FP32_FORCE = 1
+MD_MAX_N = (1 << 26) - 1
+
+_ERRNAMES = {v: k for k, v in dict(MD_ERR_ARG=-1, MD_ERR_OOM=-2, MD_ERR_LIST_OVERFLOW=-3,
+                                   MD_ERR_NONFINITE=-4, MD_ERR_TIMEOUT=-5, MD_ERR_CUDA=-6,
+                                   MD_ERR_STATE=-7).items()}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libljmd.so")
+
+_lib = None
+_P = C.c_void_p
+_PD = C.POINTER(C.c_double)
+_PI64 = C.POINTER(C.c_int64)
+_PI32 = C.POINTER(C.c_int32)
+
+# name -> (restype, argtypes); mirrors include/ljmd.h
+SIGNATURES = {
+    "md_create": (C.c_int, [C.c_double, C.c_int64, C.c_double, C.c_double, C.POINTER(_P)]),
+    "md_set_precision": (C.c_int, [_P, C.c_int]),
+    "md_set_state": (C.c_int, [_P, _PD, _PD]),
+    "md_set_state_dev": (C.c_int, [_P, _P, _P, _P]),
+    "md_get_state": (C.c_int, [_P, _PD, _PD]),
+    "md_get_state_dev": (C.c_int, [_P, _P, _P, _P]),
+    "md_step": (C.c_int, [_P, C.c_int64, C.c_double]),
+    "md_step_async": (C.c_int, [_P, C.c_int64, C.c_double, _P]),
+    "md_forces": (C.c_int, [_P, _PD]),
+    "md_forces_dev": (C.c_int, [_P, _P, _P]),
+    "md_observables": (C.c_int, [_P, _PD, _PD, _PD, _PD, _PD]),
+    "md_stats": (C.c_int, [_P, _PI64, _PI64]),
+    "md_build_list": (C.c_int, [_P]),
+    "md_get_cells": (C.c_int, [_P, _PI32, _PI32]),
+    "md_list_size": (C.c_int, [_P, _PI64]),
+    "md_get_list": (C.c_int, [_P, _PI64, _PI32]),
+    "md_pair_stats": (C.c_int, [_P, _PI64, _PI64]),
+    "md_set_timing": (C.c_int, [_P, C.c_int]),
+    "md_get_timing": (C.c_int, [_P, _PD]),
+    "md_destroy": (None, [_P]),
+    "md_last_error": (C.c_char_p, []),
+    "md_version": (C.c_char_p, []),
+}
+
+
+class MDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load_library(path: str | None = None):
+    """Load (once) the CUDA library; raises if it is not built or not loadable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libljmd is not built ({path} missing); run paper_1210_3450_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != MD_OK:
+        raise MDError(code, _lib.md_last_error().decode())
+
+
+def _host3(a, n: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3)
+    if a.shape[0] != n:
+        raise ValueError(f"expected {n} rows, got {a.shape[0]}")
+    return a
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _dev_ptr(t, n: int) -> int:
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64" and t.numel() == 3 * n):
+        raise ValueError("expected a contiguous CUDA float64 tensor with N*3 elements")
+    return int(t.data_ptr())
+
+
+class LJSystem:
+    """One periodic truncated-LJ system on the current CUDA device (md_create)."""
+
+    def __init__(self, box: float, n: int, rc: float, skin: float, precision: int = MD_FP64):
+        lib = load_library()
+        h = _P()
+        _check(lib.md_create(float(box), int(n), float(rc), float(skin), C.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.box = float(box)
+        self.rc = float(rc)
+        self.skin = float(skin)
+        if precision != MD_FP64:
+            self.set_precision(precision)
+
+    # lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.md_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # C ABI calls
+    def set_precision(self, mode: int):
+        _check(_lib.md_set_precision(self._h, int(mode)))
+
+    def set_state(self, x, v):
+        x = _host3(x, self.n)
+        v = _host3(v, self.n)
+        _check(_lib.md_set_state(self._h, _pd(x), _pd(v)))
+
+    def set_state_dev(self, x, v, stream=None):
+        _check(_lib.md_set_state_dev(self._h, _dev_ptr(x, self.n), _dev_ptr(v, self.n), _stream_ptr(stream)))
+
+    def get_state(self):
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        _check(_lib.md_get_state(self._h, _pd(x), _pd(v)))
+        return x, v
+
+    def get_state_dev(self, x=None, v=None, stream=None):
+        _check(_lib.md_get_state_dev(self._h, _dev_ptr(x, self.n) if x is not None else None,
+                                     _dev_ptr(v, self.n) if v is not None else None,
+                                     _stream_ptr(stream)))
+
+    def step(self, nsteps: int, dt: float):
+        _check(_lib.md_step(self._h, int(nsteps), float(dt)))
+
+    def step_async(self, nsteps: int, dt: float, stream=None):
+        _check(_lib.md_step_async(self._h, int(nsteps), float(dt), _stream_ptr(stream)))
+
+    def forces(self) -> np.ndarray:
+        f = np.empty((self.n, 3))
+        _check(_lib.md_forces(self._h, _pd(f)))
+        return f
+
+    def forces_dev(self, f, stream=None):
+        _check(_lib.md_forces_dev(self._h, _dev_ptr(f, self.n), _stream_ptr(stream)))
+
+    def observables(self) -> dict:
+        vals = [C.c_double() for _ in range(5)]
+        _check(_lib.md_observables(self._h, *[C.byref(v) for v in vals]))
+        return dict(zip(["pe", "virial", "ke", "temperature", "pressure"], [v.value for v in vals]))
+
+    def stats(self) -> dict:
+        r, s = C.c_int64(), C.c_int64()
+        _check(_lib.md_stats(self._h, C.byref(r), C.byref(s)))
+        return dict(rebuilds=r.value, steps=s.value)
+
+    def build_list(self):
+        _check(_lib.md_build_list(self._h))
+
+    def get_cells(self) -> tuple[np.ndarray, int]:
+        cell = np.empty(self.n, dtype=np.int32)
+        nc = C.c_int32()
+        _check(_lib.md_get_cells(self._h, cell.ctypes.data_as(_PI32), C.byref(nc)))
+        return cell, nc.value
+
+    def list_size(self) -> int:
+        t = C.c_int64()
+        _check(_lib.md_list_size(self._h, C.byref(t)))
+        return t.value
+
+    def pair_stats(self) -> tuple[int, int]:
+        """(listed pairs, listed pairs with r < rc at the current positions)."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(_lib.md_pair_stats(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_timing(self, on: bool = True):
+        _check(_lib.md_set_timing(self._h, 1 if on else 0))
+
+    def get_timing(self) -> dict:
+        out = np.zeros(8)
+        _check(_lib.md_get_timing(self._h, _pd(out)))
+        return dict(step_ms=out[0], step_launches=int(out[1]), list_ms=out[2],
+                    list_launches=int(out[3]), bin_ms=out[4], rebuilds=int(out[5]),
+                    launches=int(out[6]))
+
+    def get_list(self) -> tuple[np.ndarray, np.ndarray]:
+        total = self.list_size()
+        start = np.empty(self.n + 1, dtype=np.int64)
+        partners = np.empty(max(total, 1), dtype=np.int32)
+        _check(_lib.md_get_list(self._h, start.ctypes.data_as(_PI64), partners.ctypes.data_as(_PI32)))
+        return start, partners[:total]
+
+
+def version() -> str:
+    return load_library().md_version().decode()

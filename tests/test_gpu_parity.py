@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars (written in each test):
+  - cell of every particle and pair-list membership: bit-exact at identical
+    positions (integer / index results);
+  - FP64 forces: max_i |F_i - F_i^ref| / rms_i |F_i^ref| <= 1e-12;
+  - FP32-force mode: the same norm <= 1e-5;
+  - observables PE, W, KE: relative 1e-12 (FP64 sums in another order);
+  - 200-step trajectory: positions within 1e-10 and velocities within 1e-9 of
+    the oracle (a 1e-14 perturbation grows to ~1e-13 over these 200 steps in the
+    oracle itself), and identical rebuild counts.
+"""
+import numpy as np
+import pytest
+
+import lj_inputs as li
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def force_err(f, ref):
+    rms = np.sqrt((ref ** 2).sum(1).mean())
+    return np.abs(f - ref).max() / rms
+
+
+def sorted_csr(start, partners):
+    seg = np.repeat(np.arange(len(start) - 1), np.diff(start))
+    order = np.lexsort((partners, seg))
+    return partners[order]
+
+
+def make(ljmd, x, v, box, rc=2.5, skin=0.3, precision=0):
+    s = ljmd.LJSystem(box, len(x), rc, skin, precision)
+    s.set_state(x, v)
+    return s
+
+
+def configs():
+    out = []
+    x, box = li.perturbed_fcc(4000, 0.8442, 0.1, 101)
+    out.append(("perturbed-4000", x, box))
+    x, box = li.perturbed_fcc(4001, 0.8442, 0.1, 102)   # ragged last tile
+    out.append(("perturbed-4001", x, box))
+    cfg = li.config_small_fluid()
+    out.append(("fcc-4000-exact-lattice", cfg.x, cfg.box))   # sites on cell faces
+    # a 6^3 lattice exactly on the cell faces (L = 16.8, 6 cells of side 2.8 ->
+    # 5 cells of side 3.36), plus points at 0, at the largest double below L and
+    # outside the box
+    box = 16.8
+    g = np.arange(6) * (box / 6)
+    pts = np.array([[a, b, c] for a in g for b in g for c in g])
+    edge = np.nextafter(box, 0.0)
+    extra = np.array([[edge, 1.4, 1.4], [1.4, edge, 4.2], [4.2, 1.4, edge], [-1e-17, 1.4, 9.8],
+                      [16.8 + 1.4, 12.6 + 1.4, -1.4], [3.36, 3.36 + 1.4, 1.4]])
+    out.append(("cell-faces", np.concatenate([pts, extra]), box))
+    x, box = li.perturbed_fcc(518, 0.8442, 0.1, 109)     # exactly 3 cells per axis
+    out.append(("three-cells-518", x, box))
+    x, box = li.perturbed_fcc(300, 0.85, 0.1, 103)      # fewer than 3 cells per axis
+    out.append(("small-box-300", x, box))
+    x, box = li.perturbed_fcc(33, 0.1, 0.2, 104)        # one full tile + 1, all pairs
+    out.append(("dilute-33", x, box))
+    return out
+
+
+CONFIGS = configs()
+IDS = [c[0] for c in CONFIGS]
+_U = li.uniform_positions(3000, 18.0, 7)              # uniform, overlaps allowed
+LIST_CONFIGS = CONFIGS + [("uniform-3000", _U, 18.0)]
+LIST_IDS = IDS + ["uniform-3000"]
+
+
+@pytest.mark.parametrize("name,x,box", LIST_CONFIGS, ids=LIST_IDS)
+def test_wrap_cells_and_list_bit_exact(ljmd, oracle, name, x, box):
+    v = np.zeros_like(x)
+    with make(ljmd, x, v, box) as s:
+        s.build_list()
+        xg, _ = s.get_state()
+        xw = oracle.wrap(x, box)
+        np.testing.assert_array_equal(xg, xw)      # same wrap, bit for bit
+        cell, nc = s.get_cells()
+        onc = oracle.cells_per_axis(box, 2.8)
+        if onc >= 3:
+            assert nc == onc
+            np.testing.assert_array_equal(cell, oracle.cell_index(xw, box, 2.8))
+        else:
+            assert nc == 1 and np.all(cell == 0)
+        start, partners = s.get_list()
+        ostart, opartners = oracle.build_list(xw, box, 2.8)
+        np.testing.assert_array_equal(start, ostart)
+        np.testing.assert_array_equal(sorted_csr(start, partners), opartners)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, FP32_TOL)], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name,x,box", CONFIGS, ids=IDS)
+def test_forces_match_oracle(ljmd, oracle, name, x, box, precision, tol):
+    v = np.zeros_like(x)
+    with make(ljmd, x, v, box, precision=precision) as s:
+        f = s.forces()
+    ref = oracle.forces_brute(oracle.wrap(x, box), box, 2.5)
+    if np.sqrt((ref ** 2).sum(1).mean()) < 1e-9:   # perfect lattice: forces vanish
+        assert np.abs(f).max() < (1e-11 if precision == 0 else 1e-3)
+        return
+    assert force_err(f, ref) <= tol
+
+
+def test_forces_rc3_cavitation_cutoff(ljmd, oracle):
+    x, box = li.perturbed_fcc(4 * 9 ** 3, 0.70, 0.1, 105)
+    for precision, tol in [(0, FP64_TOL), (1, FP32_TOL)]:
+        with make(ljmd, x, np.zeros_like(x), box, rc=3.0, precision=precision) as s:
+            f = s.forces()
+        ref = oracle.forces(x, box, 3.0)
+        assert force_err(f, ref) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_observables_match_oracle(ljmd, oracle, precision):
+    x, box = li.perturbed_fcc(4000, 0.8442, 0.1, 106)
+    v = li.maxwell_boltzmann(4000, 0.722, 107)
+    with make(ljmd, x, v, box, precision=precision) as s:
+        o = s.observables()
+    r = oracle.observables(x, v, box, 2.5)
+    for k in ["pe", "virial", "ke", "temperature", "pressure"]:
+        assert o[k] == pytest.approx(r[k], rel=1e-12), k
+
+
+def test_trajectory_200_steps_fp64(ljmd, oracle):
+    """The N = 4000 fluid (FCC, rho 0.8442, T 0.722, dt 0.005) for 200 steps."""
+    cfg = li.config_small_fluid()
+    with make(ljmd, cfg.x, cfg.v, cfg.box) as s:
+        s.step(cfg.steps, cfg.dt)
+        xg, vg = s.get_state()
+        st = s.stats()
+        og = s.observables()
+    r = oracle.run(cfg.x, cfg.v, cfg.box, cfg.rc, cfg.skin, cfg.steps, cfg.dt)
+    d = xg - r["x"]
+    d -= cfg.box * np.round(d / cfg.box)
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(vg - r["v"]).max() < 1e-9
+    assert st["rebuilds"] == r["rebuilds"]
+    assert st["steps"] == cfg.steps
+    ro = oracle.observables(r["x"], r["v"], cfg.box, cfg.rc)
+    assert og["pe"] == pytest.approx(ro["pe"], rel=1e-10)
+
+
+def test_split_steps_equal_one_call(ljmd):
+    """md_step(100) equals md_step(40) + md_step(60) bit for bit (forces kept
+    between calls, same rebuild points)."""
+    x, box = li.perturbed_fcc(2000, 0.8442, 0.08, 108)
+    v = li.maxwell_boltzmann(2000, 0.9, 109)
+    for precision in (0, 1):
+        with make(ljmd, x, v, box, precision=precision) as a, make(ljmd, x, v, box, precision=precision) as b:
+            a.step(100, 0.005)
+            b.step(40, 0.005)
+            b.step(60, 0.005)
+            xa, va = a.get_state()
+            xb, vb = b.get_state()
+            np.testing.assert_array_equal(xa, xb)
+            np.testing.assert_array_equal(va, vb)
+
+
+def test_fp32_trajectory_close(ljmd, oracle):
+    cfg = li.config_small_fluid()
+    with make(ljmd, cfg.x, cfg.v, cfg.box, precision=1) as s:
+        s.step(20, cfg.dt)
+        xg, vg = s.get_state()
+    r = oracle.run(cfg.x, cfg.v, cfg.box, cfg.rc, cfg.skin, 20, cfg.dt)
+    d = xg - r["x"]
+    d -= cfg.box * np.round(d / cfg.box)
+    assert np.abs(d).max() < 1e-6
+    assert np.abs(vg - r["v"]).max() < 1e-4
+
+
+def test_list_overflow_grows_capacity(ljmd, oracle):
+    """Particles packed into one corner exceed the initial list capacity; the
+    library grows it and the list still matches the oracle exactly."""
+    box = 20.0
+    x = li.uniform_positions(1500, 6.0, 110)
+    with make(ljmd, x, np.zeros_like(x), box) as s:
+        start, partners = s.get_list()
+    ostart, opartners = oracle.build_list(x, box, 2.8)
+    np.testing.assert_array_equal(start, ostart)
+    np.testing.assert_array_equal(sorted_csr(start, partners), opartners)
+
+
+def test_single_particle_and_dimer(ljmd, oracle):
+    with make(ljmd, np.array([[1.0, 2.0, 3.0]]), np.zeros((1, 3)), 10.0) as s:
+        assert np.all(s.forces() == 0.0)
+        s.step(3, 0.005)
+    x = np.array([[5.0, 5.0, 5.0], [6.1, 5.0, 5.0]])
+    with make(ljmd, x, np.zeros_like(x), 10.0) as s:
+        f = s.forces()
+    np.testing.assert_allclose(f, oracle.forces_brute(x, 10.0, 2.5), rtol=1e-13, atol=1e-15)
+
+
+def test_errors(ljmd):
+    with pytest.raises(ljmd.MDError) as e:
+        ljmd.LJSystem(5.0, 100, 2.5, 0.3)          # box < 2 (rc + skin)
+    assert e.value.code == ljmd.MD_ERR_ARG
+    with pytest.raises(ljmd.MDError) as e:
+        ljmd.LJSystem(20.0, 0, 2.5, 0.3)
+    assert e.value.code == ljmd.MD_ERR_ARG
+    s = ljmd.LJSystem(20.0, 10, 2.5, 0.3)
+    with pytest.raises(ljmd.MDError) as e:
+        s.step(1, 0.005)                             # no state yet
+    assert e.value.code == ljmd.MD_ERR_STATE
+    x = li.uniform_positions(10, 20.0, 111)
+    v = np.zeros_like(x)
+    v[3, 0] = np.nan
+    s.set_state(x, v)
+    with pytest.raises(ljmd.MDError) as e:
+        s.step(2, 0.005)
+    assert e.value.code == ljmd.MD_ERR_NONFINITE
+    s.close()
+
+
+def test_full_size_sampled_forces(ljmd, oracle):
+    """N = 2,048,000 (FCC 80^3 x 4, rho 0.8442) displaced by up to 0.1: forces of
+    400 sampled particles against direct all-pairs sums, both precisions, and
+    sum_i F_i ~ 0 over the whole system (full list is symmetric)."""
+    x, box = li.perturbed_fcc(2_048_000, 0.8442, 0.1, 112)
+    rng = np.random.default_rng(113)
+    idx = rng.choice(len(x), size=400, replace=False)
+    ref = np.array([oracle.force_on(x, box, 2.5, int(i)) for i in idx])
+    rms_ref = np.sqrt((ref ** 2).sum(1).mean())
+    for precision, tol in [(0, FP64_TOL), (1, FP32_TOL)]:
+        with make(ljmd, x, np.zeros_like(x), box, precision=precision) as s:
+            f = s.forces()
+            n_list = s.list_size()
+        assert np.abs(f[idx] - ref).max() / rms_ref <= tol
+        rms = np.sqrt((f ** 2).sum(1).mean())
+        assert np.abs(f.sum(0)).max() <= (1e-12 if precision == 0 else 1e-4) * len(x) * rms
+        assert 70 * len(x) < n_list < 90 * len(x)
