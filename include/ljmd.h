@@ -144,6 +144,28 @@ MD_API int md_pair_stats(md_ctx* ctx, int64_t* listed, int64_t* within_rc);
 MD_API int md_set_timing(md_ctx* ctx, int on);
 MD_API int md_get_timing(md_ctx* ctx, double* out8);
 
+/* Forces without any device allocation, for callers that must not let a library
+ * allocate device memory: applications whose device memory belongs to their own
+ * allocator or pool (which has to account for every byte), and code that cannot
+ * take the device-wide synchronisation that cudaMalloc / cudaFree may cause. The
+ * paper has no counterpart of this call; it is a service of this library.
+ *   x_dev  N*3 float64 positions on the current device (any real values: wrapped
+ *          into [0, box_L) internally), read only;
+ *   f_dev  N*3 float64 output on the current device: F_i = sum over j != i with
+ *          minimum-image r < rc of (24 r^-8 - 48 r^-14 + 8 c2)(x_j - x_i) (Eq. 1),
+ *          the same forces as md_forces (no pair list; cells of side >= rc);
+ *   stream cudaStream_t as void* (NULL = legacy default stream); the call only
+ *          enqueues work on it and returns without synchronising.
+ * Limits: 1 <= N <= 65536, rc > 0, 2 rc < box_L <= 10000; larger N returns MD_ERR_ARG.
+ * Working memory is one fixed 2.75 MiB device array inside the library (every GPU
+ * that loads the library holds it until the process exits); nothing is allocated.
+ * The first call on a device looks up that array's device address with that device
+ * current; make this first call before any stream capture. All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. Errors: MD_ERR_ARG, MD_ERR_CUDA. */
+MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, double rc,
+                             double* f_dev, void* stream);
+
 /* Release all resources of ctx (NULL is ignored). */
 MD_API void md_destroy(md_ctx* ctx);
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "md_pair_stats": (C.c_int, [_P, _PI64, _PI64]),
     "md_set_timing": (C.c_int, [_P, C.c_int]),
     "md_get_timing": (C.c_int, [_P, _PD]),
+    "md_forces_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "md_destroy": (None, [_P]),
     "md_last_error": (C.c_char_p, []),
     "md_version": (C.c_char_p, []),
@@ -233,6 +234,15 @@ class LJSystem:
         partners = np.empty(max(total, 1), dtype=np.int32)
         _check(_lib.md_get_list(self._h, start.ctypes.data_as(_PI64), partners.ctypes.data_as(_PI32)))
         return start, partners[:total]
+
+
+def forces_noalloc(x, box: float, rc: float, f, stream=None):
+    """md_forces_noalloc: forces of the positions in CUDA tensor x (N x 3, float64)
+    into CUDA tensor f, using the library's fixed scratch array (no allocation;
+    N <= 65536). Work is enqueued on stream (None = legacy default stream)."""
+    n = x.numel() // 3
+    _check(load_library().md_forces_noalloc(_dev_ptr(x, n), n, float(box), float(rc),
+                                            _dev_ptr(f, n), _stream_ptr(stream)))
 
 
 def version() -> str:
