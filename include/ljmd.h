@@ -169,6 +169,80 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
 /* Release all resources of ctx (NULL is ignored). */
 MD_API void md_destroy(md_ctx* ctx);
 
+/* ------------------------------------------------------------ many systems
+ * A batch is one device-resident arena holding many independent systems (replicas
+ * of uneven size). Every kernel of a step covers all active systems of the batch
+ * in one launch (one warp per 32-particle tile, each tile belonging to one system),
+ * so a step of the whole batch costs one launch per kernel, not one per system.
+ * Systems can be added to and removed from free arena ranges between steps
+ * (continuous batching). Each system keeps its own box, cutoff, skin, time step,
+ * pair list, list-validity check and rebuild counter; results of a system do not
+ * depend on the other systems in the batch (no cross-system arithmetic, fixed
+ * per-system reduction order). Ids are small integers in [0, max_systems). */
+typedef struct md_batch md_batch;
+
+typedef struct md_sys_desc {
+  int64_t N;    /* particles                         */
+  double box_L; /* cubic box side                    */
+  double rc;    /* cutoff of Eq. 1                   */
+  double skin;  /* list margin (list radius rc+skin) */
+} md_sys_desc;
+
+/* Batch holding exactly nsys systems with ids 0..nsys-1 (arena sized to fit them).
+ * Same limits per system as md_create. */
+MD_API int md_batch_create(int nsys, const md_sys_desc* desc, int precision, md_batch** out);
+
+/* Empty arena with capacities: particle slots, cell entries, pair-list words and
+ * system records (see md_batch_footprint for what one system needs). */
+MD_API int md_batch_create_arena(int64_t slots, int64_t cells, int64_t list_words, int max_systems,
+                                 int precision, md_batch** out);
+
+/* Arena space one system needs (particle slots, cell entries, list words);
+ * validates desc like md_create. */
+MD_API int md_batch_footprint(const md_sys_desc* desc, int64_t* slots, int64_t* cells,
+                              int64_t* list_words);
+
+/* Add a system in free arena ranges; *id receives its id. MD_ERR_OOM if it does not
+ * fit (the batch is unchanged). The new system is active and needs a state. */
+MD_API int md_batch_add(md_batch* b, const md_sys_desc* desc, int* id);
+
+/* Remove a system and return its ranges to the arena. */
+MD_API int md_batch_remove(md_batch* b, int id);
+
+/* out8: slots capacity, slots free, cells capacity, cells free, list words capacity,
+ * list words free, system records, systems in use. */
+MD_API int md_batch_usage(md_batch* b, int64_t* out8);
+
+/* Include (on = 1) or exclude (on = 0) a system from md_batch_step. */
+MD_API int md_batch_set_active(md_batch* b, int id, int on);
+
+MD_API int md_batch_set_precision(md_batch* b, int mode);
+
+/* Per-system state transfer, same conventions as md_set_state / md_get_state. */
+MD_API int md_batch_set_state(md_batch* b, int id, const double* x, const double* v);
+MD_API int md_batch_set_state_dev(md_batch* b, int id, const double* x_dev, const double* v_dev,
+                                  void* stream);
+MD_API int md_batch_get_state(md_batch* b, int id, double* x, double* v);
+MD_API int md_batch_get_state_dev(md_batch* b, int id, double* x_dev, double* v_dev, void* stream);
+
+/* Advance every active system by nsteps velocity-Verlet steps; dt[id] is the time
+ * step of system id (an array of max_systems doubles; entries of inactive ids are
+ * ignored). Blocks until done. */
+MD_API int md_batch_step(md_batch* b, int64_t nsteps, const double* dt);
+MD_API int md_batch_step_async(md_batch* b, int64_t nsteps, const double* dt, void* stream);
+
+/* Forces of one system at its current positions (N*3 host array). */
+MD_API int md_batch_forces(md_batch* b, int id, double* f);
+
+/* Observables of every active system: out[5 * id + {0..4}] = pe, virial, ke, T, P
+ * (as md_observables); out holds 5 * max_systems doubles (inactive ids get zeros). */
+MD_API int md_batch_observables(md_batch* b, double* out);
+
+MD_API int md_batch_stats(md_batch* b, int id, int64_t* rebuilds, int64_t* steps);
+MD_API int md_batch_set_timing(md_batch* b, int on);
+MD_API int md_batch_get_timing(md_batch* b, double* out8);
+MD_API void md_batch_destroy(md_batch* b);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 MD_API const char* md_last_error(void);
 

@@ -3,5 +3,5 @@
 The compute path is the CUDA library built from ``csrc/`` (see ``build.py``);
 ``ljmd`` is its Python binding.
 """
-from .ljmd import (LJSystem, MDError, MD_FP32_FORCE, MD_FP64, MD_MAX_N, load_library,  # noqa: F401
-                   version)
+from .ljmd import (LJBatch, LJSystem, MDError, MD_FP32_FORCE, MD_FP64, MD_MAX_N,  # noqa: F401
+                   footprint, load_library, version)

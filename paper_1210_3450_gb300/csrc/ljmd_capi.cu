@@ -91,7 +91,8 @@ int md_set_state(md_ctx* c, const double* x, const double* v) {
     return MD_ERR_ARG;
   }
   const int64_t n = n_of(c);
-  double* st = c->eng.stage();
+  double* st = nullptr;
+  if ((r = c->eng.stage(n, &st))) return r;
   if ((r = h2d(c, st, x, 3 * n))) return r;
   if ((r = h2d(c, st + 3 * n, v, 3 * n))) return r;
   if ((r = c->eng.set_state_dev(0, st, st + 3 * n, c->stream))) return r;
@@ -113,7 +114,8 @@ int md_get_state(md_ctx* c, double* x, double* v) {
   int r = check_ctx(c);
   if (r) return r;
   const int64_t n = n_of(c);
-  double* st = c->eng.stage();
+  double* st = nullptr;
+  if ((r = c->eng.stage(n, &st))) return r;
   if ((r = c->eng.get_state_dev(0, x ? st : nullptr, v ? st + 3 * n : nullptr, c->stream))) return r;
   if (x && (r = d2h(c, x, st, 3 * n))) return r;
   if (v && (r = d2h(c, v, st + 3 * n, 3 * n))) return r;
@@ -147,7 +149,8 @@ int md_forces(md_ctx* c, double* f) {
     set_error("null force array");
     return MD_ERR_ARG;
   }
-  double* st = c->eng.stage();
+  double* st = nullptr;
+  if ((r = c->eng.stage(n_of(c), &st))) return r;
   if ((r = c->eng.forces_dev(0, st, c->stream))) return r;
   return d2h(c, f, st, 3 * n_of(c));
 }
@@ -255,6 +258,300 @@ void md_destroy(md_ctx* c) {
 }
 
 const char* md_last_error(void) { return ljmd::last_error_cstr(); }
+
+// ----------------------------------------------------------------- batches
+
+struct md_batch {
+  ljmd::Engine eng;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+int check_batch(md_batch* b) {
+  if (!b) {
+    set_error("null batch");
+    return MD_ERR_ARG;
+  }
+  set_error("");
+  return MD_OK;
+}
+
+int check_id(md_batch* b, int id) {
+  if (!b->eng.valid_id(id)) {
+    set_error("no such system id");
+    return MD_ERR_ARG;
+  }
+  return MD_OK;
+}
+
+int new_batch(md_batch** out, md_batch** b) {
+  if (!out) {
+    set_error("null output handle");
+    return MD_ERR_ARG;
+  }
+  *out = nullptr;
+  *b = new (std::nothrow) md_batch();
+  if (!*b) {
+    set_error("host allocation failed");
+    return MD_ERR_OOM;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&(*b)->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete *b;
+    *b = nullptr;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  return MD_OK;
+}
+
+int finish_batch(int r, md_batch* b, md_batch** out) {
+  if (r != MD_OK) {
+    std::string msg = ljmd::last_error_cstr();
+    cudaStreamDestroy(b->stream);
+    delete b;
+    set_error(msg);
+    return r;
+  }
+  *out = b;
+  return MD_OK;
+}
+
+ljmd::SysSpec spec_of(const md_sys_desc& d) { return ljmd::SysSpec{d.N, d.box_L, d.rc, d.skin}; }
+
+int bh2d(md_batch* b, double* dst, const double* src, int64_t count) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)count, cudaMemcpyHostToDevice, b->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "host to device copy");
+}
+
+int bd2h(md_batch* b, double* dst, const double* src, int64_t count) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+  e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "stream synchronize");
+}
+}  // namespace
+
+int md_batch_create(int nsys, const md_sys_desc* desc, int precision, md_batch** out) {
+  set_error("");
+  if (nsys <= 0 || !desc) {
+    set_error("need nsys > 0 and a descriptor array");
+    return MD_ERR_ARG;
+  }
+  md_batch* b = nullptr;
+  int r = new_batch(out, &b);
+  if (r) return r;
+  std::vector<ljmd::SysSpec> specs;
+  for (int k = 0; k < nsys; ++k) specs.push_back(spec_of(desc[k]));
+  return finish_batch(b->eng.init(specs, precision), b, out);
+}
+
+int md_batch_create_arena(int64_t slots, int64_t cells, int64_t list_words, int max_systems, int precision,
+                          md_batch** out) {
+  set_error("");
+  md_batch* b = nullptr;
+  int r = new_batch(out, &b);
+  if (r) return r;
+  ljmd::ArenaCaps caps{slots, cells, list_words, max_systems};
+  return finish_batch(b->eng.init_arena(caps, precision), b, out);
+}
+
+int md_batch_footprint(const md_sys_desc* desc, int64_t* slots, int64_t* cells, int64_t* list_words) {
+  set_error("");
+  if (!desc) {
+    set_error("null descriptor");
+    return MD_ERR_ARG;
+  }
+  ljmd::SysFootprint f;
+  int r = ljmd::footprint(spec_of(*desc), &f, nullptr);
+  if (r) return r;
+  if (slots) *slots = f.slots;
+  if (cells) *cells = f.cells;
+  if (list_words) *list_words = f.list_words;
+  return MD_OK;
+}
+
+int md_batch_add(md_batch* b, const md_sys_desc* desc, int* id) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!desc || !id) {
+    set_error("null argument");
+    return MD_ERR_ARG;
+  }
+  return b->eng.add_system(spec_of(*desc), id);
+}
+
+int md_batch_remove(md_batch* b, int id) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return b->eng.remove_system(id);
+}
+
+int md_batch_usage(md_batch* b, int64_t* out8) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!out8) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  b->eng.arena_usage(out8);
+  return MD_OK;
+}
+
+int md_batch_set_active(md_batch* b, int id, int on) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_active(id, on != 0);
+}
+
+int md_batch_set_precision(md_batch* b, int mode) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_precision(mode);
+}
+
+int md_batch_set_state(md_batch* b, int id, const double* x, const double* v) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  if (!x || !v) {
+    set_error("null state array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = b->eng.sys(id).spec.n;
+  double* st = nullptr;
+  if ((r = b->eng.stage(n, &st))) return r;
+  if ((r = bh2d(b, st, x, 3 * n))) return r;
+  if ((r = bh2d(b, st + 3 * n, v, 3 * n))) return r;
+  if ((r = b->eng.set_state_dev(id, st, st + 3 * n, b->stream))) return r;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? MD_OK : cuda_fail(e, "stream synchronize");
+}
+
+int md_batch_set_state_dev(md_batch* b, int id, const double* x, const double* v, void* stream) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!x || !v) {
+    set_error("null state array");
+    return MD_ERR_ARG;
+  }
+  return b->eng.set_state_dev(id, x, v, (cudaStream_t)stream);
+}
+
+int md_batch_get_state(md_batch* b, int id, double* x, double* v) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  const int64_t n = b->eng.sys(id).spec.n;
+  double* st = nullptr;
+  if ((r = b->eng.stage(n, &st))) return r;
+  if ((r = b->eng.get_state_dev(id, x ? st : nullptr, v ? st + 3 * n : nullptr, b->stream))) return r;
+  if (x && (r = bd2h(b, x, st, 3 * n))) return r;
+  if (v && (r = bd2h(b, v, st + 3 * n, 3 * n))) return r;
+  return MD_OK;
+}
+
+int md_batch_get_state_dev(md_batch* b, int id, double* x, double* v, void* stream) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.get_state_dev(id, x, v, (cudaStream_t)stream);
+}
+
+int md_batch_step_async(md_batch* b, int64_t nsteps, const double* dt, void* stream) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!dt) {
+    set_error("null dt array");
+    return MD_ERR_ARG;
+  }
+  std::vector<double> dts(dt, dt + b->eng.nsys());
+  return b->eng.step(nsteps, dts, (cudaStream_t)stream);
+}
+
+int md_batch_step(md_batch* b, int64_t nsteps, const double* dt) {
+  int r = check_batch(b);
+  if (r) return r;
+  return md_batch_step_async(b, nsteps, dt, b->stream);
+}
+
+int md_batch_forces(md_batch* b, int id, double* f) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  if (!f) {
+    set_error("null force array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = b->eng.sys(id).spec.n;
+  double* st = nullptr;
+  if ((r = b->eng.stage(n, &st))) return r;
+  if ((r = b->eng.forces_dev(id, st, b->stream))) return r;
+  return bd2h(b, f, st, 3 * n);
+}
+
+int md_batch_observables(md_batch* b, double* out) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!out) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  const int ns = b->eng.nsys();
+  std::vector<double> o3((size_t)(3 * ns));
+  if ((r = b->eng.observables(o3.data(), b->stream))) return r;
+  for (int k = 0; k < ns; ++k) {
+    double* q = out + 5 * k;
+    const ljmd::SysHost& h = b->eng.sys(k);
+    if (!h.used || !h.active) {
+      for (int m = 0; m < 5; ++m) q[m] = 0.0;
+      continue;
+    }
+    const int64_t n = h.spec.n;
+    const double L = h.spec.L;
+    q[0] = o3[3 * k + 0];
+    q[1] = o3[3 * k + 1];
+    q[2] = o3[3 * k + 2];
+    q[3] = n > 1 ? 2.0 * q[2] / (3.0 * (double)(n - 1)) : 0.0;
+    q[4] = (2.0 * q[2] + q[1]) / (3.0 * L * L * L);
+  }
+  return MD_OK;
+}
+
+int md_batch_stats(md_batch* b, int id, int64_t* rebuilds, int64_t* steps) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  if (rebuilds) *rebuilds = b->eng.sys(id).rebuilds;
+  if (steps) *steps = b->eng.sys(id).steps;
+  return MD_OK;
+}
+
+int md_batch_set_timing(md_batch* b, int on) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_timing(on != 0);
+}
+
+int md_batch_get_timing(md_batch* b, double* out8) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!out8) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  b->eng.get_timing(out8);
+  return MD_OK;
+}
+
+void md_batch_destroy(md_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  cudaStream_t s = b->stream;
+  delete b;
+  if (s) cudaStreamDestroy(s);
+}
 
 const char* md_version(void) { return "ljmd 0.1 (sm_103a)"; }
 

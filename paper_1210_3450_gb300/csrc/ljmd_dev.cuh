@@ -6,11 +6,12 @@
 // neighbour loads). A warp owns one tile of 32 consecutive slots of one system.
 //
 // Pair list (Sec. 2.1 "sorted pair list", Fig. 1) in a transposed key-pointer form:
-// the partners of the particle in lane l of tile t are entries
-//     nbr[list_off + (t_local * kmax + k) * 32 + l],  k < ncnt[slot],
-// so one warp reads 32 consecutive words per k. An entry packs the partner's
-// slot index relative to the system (bits 0..25) and the periodic image of the
-// partner (bits 26..31: two bits per axis, 0 = same image, 1 = +L, 2 = -L).
+// the partners of the particle in lane l of tile t are grouped four at a time,
+//     nbr[list_off + ((t_local * kmax / 4 + k / 4) * 32 + l) * 4 + k % 4],  k < ncnt[slot],
+// so each thread reads its next four partners with one 16-byte load and a warp
+// reads 512 consecutive bytes per group. An entry packs the partner's slot index
+// relative to the system (bits 0..25) and the periodic image of the partner
+// (bits 26..31: two bits per axis, 0 = same image, 1 = +L, 2 = -L).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,6 +21,12 @@ namespace ljmd {
 constexpr int kTile = 32;
 constexpr int kIdxBits = 26;
 constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+
+// Word index of list entry k of the particle in lane `lane` of local tile tl
+// (kmax is a multiple of 8).
+__host__ __device__ inline int64_t list_word(int64_t l_off, int tl, int kmax, int lane, int k) {
+  return l_off + (((int64_t)tl * (kmax >> 2) + (k >> 2)) * kTile + lane) * 4 + (k & 3);
+}
 
 // Per-system constants (device copy), written by the host.
 struct SysParams {
@@ -66,7 +73,8 @@ enum StepFlags : int {
 struct DevArrays {
   double4_32a* x[2];      // positions (w unused), ping-pong by step parity
   double4_32a* v;         // velocities
-  double4_32a* xref;      // positions at the last list build
+  double4_32a* xref;      // positions at the last list build (FP64 form's check)
+  int4* xqref;        // shadow positions at the last list build (FP32-force form's check)
   double4_32a* f;         // stored forces (double)
   int4* xq[2];        // fixed-point shadow positions (uint32 per axis, wraps at L)
   int32_t* id;        // caller index of each slot, -1 for padding

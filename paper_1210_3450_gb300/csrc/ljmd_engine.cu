@@ -144,125 +144,315 @@ void Engine::collect_timing() {
   ev_pending_.clear();
 }
 
+// ------------------------------------------------------------- ranges
+
+void RangeAlloc::reset(int64_t cap) {
+  cap_ = cap;
+  free_.clear();
+  if (cap > 0) free_[0] = cap;
+}
+
+int64_t RangeAlloc::alloc(int64_t len) {
+  if (len <= 0) len = 1;
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second >= len) {
+      const int64_t off = it->first, rest = it->second - len;
+      free_.erase(it);
+      if (rest > 0) free_[off + len] = rest;
+      return off;
+    }
+  }
+  return -1;
+}
+
+void RangeAlloc::release(int64_t off, int64_t len) {
+  if (len <= 0) len = 1;
+  auto it = free_.emplace(off, len).first;
+  auto nx = std::next(it);
+  if (nx != free_.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    free_.erase(nx);
+  }
+  if (it != free_.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      free_.erase(it);
+    }
+  }
+}
+
+void RangeAlloc::grow(int64_t new_cap) {
+  if (new_cap <= cap_) return;
+  const int64_t old = cap_;
+  cap_ = new_cap;
+  release(old, new_cap - old);
+}
+
+int64_t RangeAlloc::free_total() const {
+  int64_t t = 0;
+  for (const auto& kv : free_) t += kv.second;
+  return t;
+}
+
+int64_t RangeAlloc::largest_free() const {
+  int64_t m = 0;
+  for (const auto& kv : free_) m = std::max(m, kv.second);
+  return m;
+}
+
+int footprint(const SysSpec& s, SysFootprint* f, SysHost* h) {
+  if (!(s.n > 0) || s.n > ((1 << 26) - 1)) { set_error("N must be in [1, 2^26 - 1]"); return kErrArg; }
+  if (!(s.rc > 0.0) || !(s.skin >= 0.0) || !std::isfinite(s.rc) || !std::isfinite(s.skin)) {
+    set_error("rc must be > 0 and skin >= 0");
+    return kErrArg;
+  }
+  if (!(s.L > 2.0 * (s.rc + s.skin)) || !(s.L <= 10000.0)) {
+    set_error("box side must satisfy 2 (rc + skin) < L <= 10000");
+    return kErrArg;
+  }
+  SysHost t;
+  t.spec = s;
+  t.rl = s.rc + s.skin;
+  // Eq. 1: V(rc) = V'(rc) = 0
+  const double irc2 = 1.0 / (s.rc * s.rc);
+  const double irc6 = irc2 * irc2 * irc2;
+  t.c2 = 6.0 * irc6 * irc6 * irc2 - 3.0 * irc6 * irc2;
+  t.c0 = 4.0 * irc6 - 7.0 * irc6 * irc6;
+  t.nc = cells_per_axis(s.L, t.rl);
+  t.ncell = (int64_t)t.nc * t.nc * t.nc;
+  t.kmax = initial_kmax(s, t.rl);
+  t.ntiles = (int32_t)((s.n + kTile - 1) / kTile);
+  if (f) {
+    f->slots = (int64_t)t.ntiles * kTile;
+    f->cells = t.ncell + 1;
+    f->list_words = (int64_t)t.ntiles * t.kmax * kTile;
+  }
+  if (h) *h = t;
+  return kOK;
+}
+
+// ------------------------------------------------------------- arena
+
 void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
-  dfree(d_.v); dfree(d_.xref); dfree(d_.f); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
+  dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.ccount); dfree(d_.cstart);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_);
   d_ = DevArrays{};
+  stage_n_ = 0;
 }
 
 int Engine::init(const std::vector<SysSpec>& specs, int precision) {
   if (specs.empty()) { set_error("no systems"); return kErrArg; }
-  if (precision != 0 && precision != 1) { set_error("unknown precision mode"); return kErrArg; }
-  precision_ = precision;
-  sys_.clear();
-  int64_t p = 0, c = 0, l = 0;
-  int32_t t = 0;
-  stage_n_ = 0;
-  max_cells_ = 1;
+  ArenaCaps caps{0, 0, 0, (int)specs.size()};
   for (const SysSpec& s : specs) {
-    if (!(s.n > 0) || s.n > ((1 << 26) - 1)) { set_error("N must be in [1, 2^26 - 1]"); return kErrArg; }
-    if (!(s.rc > 0.0) || !(s.skin >= 0.0) || !std::isfinite(s.rc) || !std::isfinite(s.skin)) {
-      set_error("rc must be > 0 and skin >= 0");
-      return kErrArg;
-    }
-    if (!(s.L > 2.0 * (s.rc + s.skin)) || !(s.L <= 10000.0)) {
-      set_error("box side must satisfy 2 (rc + skin) < L <= 10000");
-      return kErrArg;
-    }
-    SysHost h;
-    h.spec = s;
-    h.rl = s.rc + s.skin;
-    // Eq. 1: V(rc) = V'(rc) = 0
-    const double irc2 = 1.0 / (s.rc * s.rc);
-    const double irc6 = irc2 * irc2 * irc2;
-    h.c2 = 6.0 * irc6 * irc6 * irc2 - 3.0 * irc6 * irc2;
-    h.c0 = 4.0 * irc6 - 7.0 * irc6 * irc6;
-    h.nc = cells_per_axis(s.L, h.rl);
-    h.ncell = (int64_t)h.nc * h.nc * h.nc;
-    h.kmax = initial_kmax(s, h.rl);
-    h.ntiles = (int32_t)((s.n + kTile - 1) / kTile);
-    h.p_off = p;
-    h.t_off = t;
-    h.c_off = c;
-    h.l_off = l;
-    p += (int64_t)h.ntiles * kTile;
-    t += h.ntiles;
-    c += h.ncell + 1;
-    l += (int64_t)h.ntiles * h.kmax * kTile;
-    max_cells_ = std::max(max_cells_, h.ncell);
-    stage_n_ = std::max(stage_n_, s.n);
-    sys_.push_back(h);
+    SysFootprint f;
+    CKR(footprint(s, &f, nullptr));
+    caps.slots += f.slots;
+    caps.cells += f.cells;
+    caps.list_words += f.list_words;
   }
-  nslots_ = p;
-  ntiles_ = t;
-  ncells_ = c;
-  nlist_ = l;
-  return alloc_all();
+  CKR(init_arena(caps, precision));
+  list_growable_ = true;
+  for (const SysSpec& s : specs) {
+    int id = -1;
+    CKR(add_system(s, &id));
+  }
+  return kOK;
 }
 
-int Engine::alloc_all() {
+int Engine::init_arena(const ArenaCaps& caps, int precision) {
+  if (precision != 0 && precision != 1) { set_error("unknown precision mode"); return kErrArg; }
+  if (caps.slots <= 0 || caps.cells <= 0 || caps.list_words <= 0 || caps.max_systems <= 0) {
+    set_error("arena capacities must be positive");
+    return kErrArg;
+  }
+  precision_ = precision;
+  caps_ = caps;
+  list_growable_ = false;
+  caps_.slots = round_up(caps.slots, kTile);
+  caps_.list_words = round_up(caps.list_words, 4 * kTile);
+  sys_.assign((size_t)caps.max_systems, SysHost{});
+  slot_alloc_.reset(caps_.slots / kTile);  // in tiles
+  cell_alloc_.reset(caps_.cells);
+  list_alloc_.reset(caps_.list_words / (4 * kTile));  // in 128-word units
+  h_tile_sys_.assign((size_t)(caps_.slots / kTile), -1);
+  ntiles_ = 0;
+  max_cells_ = 1;
+  cur_ = 0;
+  return alloc_arrays();
+}
+
+int Engine::alloc_arrays() {
   free_all();
   const int ns = nsys();
+  const int64_t P = caps_.slots, T = caps_.slots / kTile;
   for (int b = 0; b < 2; ++b) {
-    CKR(dmalloc(&d_.x[b], nslots_));
-    CKR(dmalloc(&d_.xq[b], nslots_));
-    CK(cudaMemset(d_.x[b], 0, sizeof(double4_32a) * nslots_));
-    CK(cudaMemset(d_.xq[b], 0, sizeof(int4) * nslots_));
+    CKR(dmalloc(&d_.x[b], P));
+    CKR(dmalloc(&d_.xq[b], P));
+    CK(cudaMemset(d_.x[b], 0, sizeof(double4_32a) * P));
+    CK(cudaMemset(d_.xq[b], 0, sizeof(int4) * P));
   }
-  CKR(dmalloc(&d_.v, nslots_));
-  CKR(dmalloc(&d_.xref, nslots_));
-  CKR(dmalloc(&d_.f, nslots_));
-  CKR(dmalloc(&d_.id, nslots_));
-  CKR(dmalloc(&d_.cell, nslots_));
-  CKR(dmalloc(&d_.ncnt, nslots_));
-  CKR(dmalloc(&d_.nbr, nlist_));
-  CKR(dmalloc(&d_.tile_obs, 3 * (int64_t)ntiles_));
-  CKR(dmalloc(&d_.xtmp, nslots_));
-  CKR(dmalloc(&d_.vtmp, nslots_));
-  CKR(dmalloc(&d_.idtmp, nslots_));
-  CKR(dmalloc(&d_.celltmp, nslots_));
-  CKR(dmalloc(&d_.perm, nslots_));
-  CKR(dmalloc(&d_.ccount, ncells_));
-  CKR(dmalloc(&d_.cstart, ncells_));
-  CK(cudaMemset(d_.v, 0, sizeof(double4_32a) * nslots_));
-  CK(cudaMemset(d_.f, 0, sizeof(double4_32a) * nslots_));
-  CK(cudaMemset(d_.xref, 0, sizeof(double4_32a) * nslots_));
-  CK(cudaMemset(d_.ncnt, 0, sizeof(int32_t) * nslots_));
-  CK(cudaMemset(d_.id, 0xff, sizeof(int32_t) * nslots_));
-  CK(cudaMemset(d_.ccount, 0, sizeof(int32_t) * ncells_));
-  CK(cudaMemset(d_.cstart, 0, sizeof(int32_t) * ncells_));
+  CKR(dmalloc(&d_.v, P));
+  CKR(dmalloc(&d_.xref, P));
+  CKR(dmalloc(&d_.xqref, P));
+  CKR(dmalloc(&d_.f, P));
+  CKR(dmalloc(&d_.id, P));
+  CKR(dmalloc(&d_.cell, P));
+  CKR(dmalloc(&d_.ncnt, P));
+  CKR(dmalloc(&d_.nbr, caps_.list_words));
+  CKR(dmalloc(&d_.tile_obs, 3 * T));
+  CKR(dmalloc(&d_.xtmp, P));
+  CKR(dmalloc(&d_.vtmp, P));
+  CKR(dmalloc(&d_.idtmp, P));
+  CKR(dmalloc(&d_.celltmp, P));
+  CKR(dmalloc(&d_.perm, P));
+  CKR(dmalloc(&d_.ccount, caps_.cells));
+  CKR(dmalloc(&d_.cstart, caps_.cells));
+  CK(cudaMemset(d_.v, 0, sizeof(double4_32a) * P));
+  CK(cudaMemset(d_.f, 0, sizeof(double4_32a) * P));
+  CK(cudaMemset(d_.xref, 0, sizeof(double4_32a) * P));
+  CK(cudaMemset(d_.ncnt, 0, sizeof(int32_t) * P));
+  CK(cudaMemset(d_.id, 0xff, sizeof(int32_t) * P));
+  CK(cudaMemset(d_.ccount, 0, sizeof(int32_t) * caps_.cells));
+  CK(cudaMemset(d_.cstart, 0, sizeof(int32_t) * caps_.cells));
   CKR(dmalloc(&d_params_, ns));
   CKR(dmalloc(&d_status_, ns));
   CKR(dmalloc(&d_disp2_, ns));
   CKR(dmalloc(&d_rebuild_, ns));
-  CKR(dmalloc(&d_tile_sys_, ntiles_));
+  CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
   CKR(dmalloc(&d_pairs_, 2 * ns));
-  CKR(dmalloc(&d_stage_, 6 * stage_n_));
   CK(cudaMemset(d_status_, 0, sizeof(SysStatus) * ns));
   CK(cudaMemset(d_disp2_, 0, sizeof(unsigned long long) * ns));
+  CK(cudaMemset(d_rebuild_, 0, sizeof(int32_t) * ns));
+  CK(cudaMemset(d_tile_sys_, 0xff, sizeof(int32_t) * T));
   CK(cudaMallocHost((void**)&h_status_, sizeof(SysStatus) * ns));
   CK(cudaMallocHost((void**)&h_disp2_, sizeof(unsigned long long) * ns));
   CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * ns));
   CK(cudaMallocHost((void**)&h_obs_, sizeof(double) * 3 * ns));
-  std::vector<int32_t> ts((size_t)ntiles_);
-  for (int k = 0; k < ns; ++k)
-    for (int q = 0; q < sys_[k].ntiles; ++q) ts[(size_t)(sys_[k].t_off + q)] = k;
-  CK(cudaMemcpy(d_tile_sys_, ts.data(), sizeof(int32_t) * ts.size(), cudaMemcpyHostToDevice));
   return upload_params();
 }
 
-int Engine::upload_params() {
-  std::vector<SysParams> ps((size_t)nsys());
-  for (int k = 0; k < nsys(); ++k) {
+int Engine::stage(int64_t n, double** out) {
+  if (n > stage_n_) {
+    dfree(d_stage_);
+    stage_n_ = 0;
+    CKR(dmalloc(&d_stage_, 6 * n));
+    stage_n_ = n;
+  }
+  *out = d_stage_;
+  return kOK;
+}
+
+void Engine::update_extent() {
+  int32_t last = 0;
+  max_cells_ = 1;
+  for (const SysHost& h : sys_) {
+    if (!h.used) continue;
+    last = std::max(last, h.t_off + h.ntiles);
+    max_cells_ = std::max(max_cells_, h.ncell);
+  }
+  ntiles_ = last;
+}
+
+int Engine::grow_list_arena(int64_t min_extra_units) {
+  const int64_t old_units = list_alloc_.cap();
+  const int64_t new_units = std::max(old_units + old_units / 2, old_units + min_extra_units);
+  uint32_t* nb = nullptr;
+  CKR(dmalloc(&nb, new_units * 4 * kTile));
+  CK(cudaMemcpy(nb, d_.nbr, sizeof(uint32_t) * old_units * 4 * kTile, cudaMemcpyDeviceToDevice));
+  dfree(d_.nbr);
+  d_.nbr = nb;
+  list_alloc_.grow(new_units);
+  caps_.list_words = new_units * 4 * kTile;
+  return kOK;
+}
+
+int Engine::upload_tiles(int k, int32_t value) {
+  const SysHost& h = sys_[k];
+  for (int q = 0; q < h.ntiles; ++q) h_tile_sys_[(size_t)(h.t_off + q)] = value;
+  CK(cudaMemcpy(d_tile_sys_ + h.t_off, h_tile_sys_.data() + h.t_off, sizeof(int32_t) * h.ntiles,
+                cudaMemcpyHostToDevice));
+  return kOK;
+}
+
+int Engine::add_system(const SysSpec& s, int* id) {
+  SysHost h;
+  SysFootprint f;
+  CKR(footprint(s, &f, &h));
+  int k = -1;
+  for (int q = 0; q < nsys(); ++q)
+    if (!sys_[q].used) { k = q; break; }
+  if (k < 0) { set_error("arena: no free system record"); return kErrOOM; }
+  const int64_t t0 = slot_alloc_.alloc(f.slots / kTile);
+  if (t0 < 0) { set_error("arena: not enough free particle slots"); return kErrOOM; }
+  const int64_t c0 = cell_alloc_.alloc(f.cells);
+  if (c0 < 0) {
+    slot_alloc_.release(t0, f.slots / kTile);
+    set_error("arena: not enough free cell entries");
+    return kErrOOM;
+  }
+  const int64_t l0 = list_alloc_.alloc(f.list_words / (4 * kTile));
+  if (l0 < 0) {
+    slot_alloc_.release(t0, f.slots / kTile);
+    cell_alloc_.release(c0, f.cells);
+    set_error("arena: not enough free list words");
+    return kErrOOM;
+  }
+  h.used = true;
+  h.active = true;
+  h.t_off = (int32_t)t0;
+  h.p_off = t0 * kTile;
+  h.c_off = c0;
+  h.l_off = l0 * 4 * kTile;
+  sys_[k] = h;
+  // cell counters of the new range must start at zero
+  CK(cudaMemset(d_.ccount + h.c_off, 0, sizeof(int32_t) * (h.ncell + 1)));
+  CKR(upload_tiles(k, k));
+  update_extent();
+  CKR(upload_params(k));
+  *id = k;
+  return kOK;
+}
+
+int Engine::remove_system(int k) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  SysHost& h = sys_[k];
+  CKR(upload_tiles(k, -1));
+  slot_alloc_.release(h.t_off, h.ntiles);
+  cell_alloc_.release(h.c_off, h.ncell + 1);
+  list_alloc_.release(h.l_off / (4 * kTile), (int64_t)h.ntiles * h.kmax / 4);
+  h = SysHost{};
+  update_extent();
+  return upload_params(k);
+}
+
+void Engine::arena_usage(int64_t* o) const {
+  o[0] = caps_.slots;
+  o[1] = slot_alloc_.free_total() * kTile;
+  o[2] = caps_.cells;
+  o[3] = cell_alloc_.free_total();
+  o[4] = caps_.list_words;
+  o[5] = list_alloc_.free_total() * 4 * kTile;
+  o[6] = caps_.max_systems;
+  int64_t used = 0;
+  for (const SysHost& h : sys_) used += h.used ? 1 : 0;
+  o[7] = used;
+}
+
+int Engine::upload_params(int only) {
+  const int k0 = only >= 0 ? only : 0, k1 = only >= 0 ? only + 1 : nsys();
+  std::vector<SysParams> ps((size_t)(k1 - k0));
+  for (int k = k0; k < k1; ++k) {
     const SysHost& h = sys_[k];
-    SysParams& P = ps[(size_t)k];
+    SysParams& P = ps[(size_t)(k - k0)];
     std::memset(&P, 0, sizeof(P));
+    if (!h.used) continue;
     P.L = h.spec.L;
     P.invL = 1.0 / h.spec.L;
     P.inv_cs = (double)h.nc / h.spec.L;
@@ -287,7 +477,7 @@ int Engine::upload_params() {
     P.ntiles = h.ntiles;
     P.active = h.active ? 1 : 0;
   }
-  CK(cudaMemcpy(d_params_, ps.data(), sizeof(SysParams) * ps.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_params_ + k0, ps.data(), sizeof(SysParams) * ps.size(), cudaMemcpyHostToDevice));
   return kOK;
 }
 
@@ -314,9 +504,17 @@ int Engine::set_precision(int mode) {
   return kOK;
 }
 
-void Engine::set_active(int k, bool on) { sys_[k].active = on; }
+int Engine::set_active(int k, bool on) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  if (sys_[k].active != on) {
+    sys_[k].active = on;
+    CKR(upload_params(k));
+  }
+  return kOK;
+}
 
 int Engine::set_state_dev(int k, const double* x, const double* v, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   SysHost& h = sys_[k];
   launch_from_caller(arrays(), cur_, x, v, k, h.ntiles, s);
   CKL();
@@ -327,6 +525,7 @@ int Engine::set_state_dev(int k, const double* x, const double* v, cudaStream_t 
 }
 
 int Engine::get_state_dev(int k, double* x, double* v, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   SysHost& h = sys_[k];
   if (!h.has_state) { set_error("no state set"); return kErrState; }
   if (x) launch_to_caller(arrays(), cur_, 0, x, h.spec.n, k, h.ntiles, s);
@@ -373,6 +572,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
         const int64_t cap = round_up(std::max<int64_t>(h.spec.n - 1, 1), 8);
         const int64_t want = std::min<int64_t>(round_up((int64_t)(h_status_[k].overflow * 1.25) + 16, 8), cap);
         if (want <= h.kmax) { set_error("pair list overflow"); return kErrOverflow; }
+        h.old_kmax = h.kmax;
         h.kmax = (int)want;
         grow = true;
       }
@@ -385,21 +585,28 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
       }
       return kOK;
     }
-    // re-lay the list storage with the larger capacities and rebuild every
-    // active system that has a state (their old lists moved)
-    int64_t l = 0;
-    for (SysHost& h : sys_) {
-      h.l_off = l;
-      l += (int64_t)h.ntiles * h.kmax * kTile;
+    // move the grown systems' lists to larger ranges and rebuild them
+    for (int k : which) {
+      SysHost& h = sys_[k];
+      const int64_t old_units = (int64_t)h.ntiles * h.old_kmax / 4;
+      list_alloc_.release(h.l_off / (4 * kTile), old_units);
+      int64_t l0 = list_alloc_.alloc((int64_t)h.ntiles * h.kmax / 4);
+      if (l0 < 0 && list_growable_) {
+        CKR(grow_list_arena((int64_t)h.ntiles * h.kmax / 4));
+        l0 = list_alloc_.alloc((int64_t)h.ntiles * h.kmax / 4);
+      }
+      if (l0 < 0) {
+        set_error("arena: not enough free list words to grow a pair list");
+        // keep the old capacity (it fits where it was)
+        h.kmax = h.old_kmax;
+        const int64_t back = list_alloc_.alloc(old_units);
+        h.l_off = back * 4 * kTile;
+        CKR(upload_params(k));
+        return kErrOverflow;
+      }
+      h.l_off = l0 * 4 * kTile;
+      CKR(upload_params(k));
     }
-    nlist_ = l;
-    dfree(d_.nbr);
-    CKR(dmalloc(&d_.nbr, nlist_));
-    CKR(upload_params());
-    std::vector<int> all;
-    for (int k = 0; k < nsys(); ++k)
-      if (sys_[k].active && sys_[k].has_state) all.push_back(k);
-    which = all;
   }
   set_error("pair list overflow persists after growing the capacity");
   return kErrOverflow;
@@ -428,6 +635,7 @@ int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
 }
 
 int Engine::pair_stats(int k, int64_t* listed, int64_t* inside, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   if (!sys_[k].has_state) { set_error("no state set"); return kErrState; }
   CKR(ensure_lists(s));
   CK(cudaMemsetAsync(d_pairs_, 0, sizeof(unsigned long long) * 2 * nsys(), s));
@@ -467,9 +675,17 @@ int Engine::post_drift(cudaStream_t s) {
       set_error("non-finite position or velocity in system " + std::to_string(k));
       return kErrNonfinite;
     }
-    double d2;
-    std::memcpy(&d2, &h_disp2_[k], sizeof(double));
-    if (!(2.0 * std::sqrt(d2) < h.spec.skin)) which.push_back(k);
+    if (precision_ == 1) {
+      // FP32-force form: exact integer check of the fixed-point shadow, with the
+      // threshold lowered by 4 units (each shadow coordinate is within 1/2 unit)
+      const double hq = 0.5 * h.spec.skin * (4294967296.0 / h.spec.L) - 4.0;
+      const double thr = hq > 0.0 ? hq * hq : 0.0;
+      if (h_disp2_[k] == ~0ull || (double)h_disp2_[k] >= thr) which.push_back(k);
+    } else {
+      double d2;
+      std::memcpy(&d2, &h_disp2_[k], sizeof(double));
+      if (!(2.0 * std::sqrt(d2) < h.spec.skin)) which.push_back(k);
+    }
   }
   return rebuild(which, s);
 }
@@ -503,6 +719,7 @@ int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) 
 }
 
 int Engine::forces_dev(int k, double* f, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   CKR(ensure_lists(s));
   CKR(ensure_forces(s));
   launch_to_caller(arrays(), cur_, 2, f, sys_[k].spec.n, k, sys_[k].ntiles, s);
@@ -533,6 +750,7 @@ int Engine::build_lists(cudaStream_t s) {
 }
 
 int Engine::get_cells(int k, int32_t* cell, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   const SysHost& h = sys_[k];
   if (!h.has_state) { set_error("no state set"); return kErrState; }
   CKR(ensure_lists(s));
@@ -545,6 +763,7 @@ int Engine::get_cells(int k, int32_t* cell, cudaStream_t s) {
 }
 
 int Engine::list_size(int k, int64_t* total, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   const SysHost& h = sys_[k];
   if (!h.has_state) { set_error("no state set"); return kErrState; }
   CKR(ensure_lists(s));
@@ -558,6 +777,7 @@ int Engine::list_size(int k, int64_t* total, cudaStream_t s) {
 }
 
 int Engine::get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   const SysHost& h = sys_[k];
   if (!h.has_state) { set_error("no state set"); return kErrState; }
   CKR(ensure_lists(s));
@@ -577,7 +797,7 @@ int Engine::get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s) {
     const int64_t q = slot_of[(size_t)i];
     const int64_t tl = q / kTile, lane = q % kTile;
     for (int32_t m = 0; m < cnt[(size_t)q]; ++m) {
-      const uint32_t e = lw[(size_t)((tl * h.kmax + m) * kTile + lane)];
+      const uint32_t e = lw[(size_t)(list_word(0, (int)tl, h.kmax, (int)lane, m))];
       partners[start[i] + m] = id[(size_t)(e & kIdxMask)];
     }
   }

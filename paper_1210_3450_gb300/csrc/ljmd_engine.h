@@ -1,9 +1,16 @@
-// Host engine: owns the device arrays of one or more LJ systems and drives the
-// kernels of one velocity-Verlet step, the list-validity check and the rebuild.
+// Host engine: owns a device-resident arena holding any number of independent
+// LJ systems and drives the kernels of one velocity-Verlet step, the
+// list-validity check and the rebuild for all of them at once.
+//
+// The arena has fixed capacities (particle slots, cell entries, list words,
+// system records). Systems are added and removed at run time (first-fit range
+// allocation), which is what continuous batching needs: a new system takes free
+// ranges while the others keep running, and a finished one returns its ranges.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -17,19 +24,28 @@ struct SysSpec {
 };
 
 struct SysHost {
-  SysSpec spec;
+  SysSpec spec{};
+  bool used = false;
   double rl = 0, c2 = 0, c0 = 0;
   int nc = 1;
   int64_t ncell = 1;
   int kmax = 0;
+  int old_kmax = 0;
   int64_t p_off = 0, c_off = 0, l_off = 0;
   int32_t t_off = 0, ntiles = 0;
-  bool active = true;
+  bool active = false;
   bool has_state = false;
   bool force_rebuild = true;
   bool f_valid = false;
   int64_t rebuilds = 0, steps = 0;
   double dt = 0.0;
+};
+
+struct ArenaCaps {
+  int64_t slots;       // particle slots (rounded up to whole 32-slot tiles)
+  int64_t cells;       // cell-array entries (a system uses nc^3 + 1)
+  int64_t list_words;  // pair-list words
+  int max_systems;     // system records
 };
 
 // Status codes shared with the C ABI (same values as MD_*).
@@ -39,6 +55,28 @@ enum : int { kOK = 0, kErrArg = -1, kErrOOM = -2, kErrOverflow = -3, kErrNonfini
 void set_error(const std::string& msg);
 const char* last_error_cstr();
 
+// First-fit allocator of integer ranges [off, off + len) within [0, cap).
+class RangeAlloc {
+ public:
+  void reset(int64_t cap);
+  int64_t alloc(int64_t len);  // offset, or -1 if no free range is long enough
+  void release(int64_t off, int64_t len);
+  int64_t cap() const { return cap_; }
+  void grow(int64_t new_cap);  // append [cap, new_cap) as free
+  int64_t free_total() const;
+  int64_t largest_free() const;
+
+ private:
+  int64_t cap_ = 0;
+  std::map<int64_t, int64_t> free_;  // offset -> length
+};
+
+// Validates a system and derives its sizes (also used for admission checks).
+struct SysFootprint {
+  int64_t slots, cells, list_words;
+};
+int footprint(const SysSpec& s, SysFootprint* f, SysHost* h);
+
 class Engine {
  public:
   Engine() = default;
@@ -46,19 +84,29 @@ class Engine {
   Engine(const Engine&) = delete;
   Engine& operator=(const Engine&) = delete;
 
-  // Lay out and allocate all systems; returns a status code.
+  // Exact-size arena for a fixed set of systems (ids 0..n-1).
   int init(const std::vector<SysSpec>& specs, int precision);
+  // Empty arena with the given capacities.
+  int init_arena(const ArenaCaps& caps, int precision);
+  // Add a system in free ranges; kErrOOM if it does not fit (nothing changes).
+  int add_system(const SysSpec& s, int* id);
+  int remove_system(int id);
+  // out8: slots cap/free, cells cap/free, list cap/free, systems cap/used.
+  void arena_usage(int64_t* out8) const;
+
   int set_precision(int mode);
   int precision() const { return precision_; }
   int nsys() const { return (int)sys_.size(); }
   const SysHost& sys(int k) const { return sys_[k]; }
+  bool valid_id(int k) const { return k >= 0 && k < nsys() && sys_[k].used; }
 
   // State transfer for one system: device arrays of n*3 doubles in caller order.
   int set_state_dev(int k, const double* x, const double* v, cudaStream_t s);
   int get_state_dev(int k, double* x, double* v, cudaStream_t s);
   int forces_dev(int k, double* f, cudaStream_t s);
 
-  // Advance every active system by nsteps steps of its own dt.
+  // Advance every active system by nsteps steps of its own dt (dt per system id;
+  // entries of inactive ids are ignored).
   int step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s);
   // Observables (pe, virial, ke) of every active system into host out3[3 * nsys].
   int observables(double* out3, cudaStream_t s);
@@ -69,17 +117,21 @@ class Engine {
   int list_size(int k, int64_t* total, cudaStream_t s);
   int get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s);
 
-  void set_active(int k, bool on);
+  int set_active(int k, bool on);
   // Per-kernel-class device times (CUDA events on the launching stream).
   int set_timing(bool on);
   void get_timing(double* out8) const;
   int pair_stats(int k, int64_t* listed, int64_t* inside, cudaStream_t s);
-  double* stage() const { return d_stage_; }  // 6 * max n doubles of device scratch
+  // Device scratch of at least 6 * n doubles for caller-order staging.
+  int stage(int64_t n, double** out);
 
  private:
-  int alloc_all();
+  int alloc_arrays();
   void free_all();
-  int upload_params();
+  int upload_params(int only = -1);
+  int upload_tiles(int k, int32_t value);
+  int grow_list_arena(int64_t min_extra_units);
+  void update_extent();
   int rebuild(std::vector<int> which, cudaStream_t s);
   int ensure_lists(cudaStream_t s);
   int ensure_forces(cudaStream_t s);
@@ -100,13 +152,16 @@ class Engine {
   int64_t t_count_[3] = {0, 0, 0};
   int64_t n_launch_ = 0;
   int64_t n_rebuild_seq_ = 0;
-  unsigned long long* d_pairs_ = nullptr;
 
   std::vector<SysHost> sys_;
   int precision_ = 0;
   int cur_ = 0;
-  int64_t nslots_ = 0, ncells_ = 0, nlist_ = 0, max_cells_ = 1;
-  int32_t ntiles_ = 0;
+  ArenaCaps caps_{0, 0, 0, 0};
+  bool list_growable_ = false;  // exact-size arenas grow their list storage on demand
+  RangeAlloc slot_alloc_, cell_alloc_, list_alloc_;
+  int64_t max_cells_ = 1;
+  int32_t ntiles_ = 0;  // launch extent: tiles up to the last used one
+  std::vector<int32_t> h_tile_sys_;
 
   DevArrays d_{};
   SysParams* d_params_ = nullptr;
@@ -115,7 +170,8 @@ class Engine {
   int32_t* d_rebuild_ = nullptr;
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;
-  double* d_stage_ = nullptr;   // caller-order staging (3 * max n doubles x 2)
+  unsigned long long* d_pairs_ = nullptr;
+  double* d_stage_ = nullptr;
   int64_t stage_n_ = 0;
   // pinned host mirrors
   SysStatus* h_status_ = nullptr;

@@ -41,6 +41,7 @@ __device__ __forceinline__ bool tile_ctx(const DevArrays& a, TileCtx& t, SysPara
   const int lane = threadIdx.x & 31;
   if (warp >= a.ntiles) return false;
   t.sys = a.tile_sys[warp];
+  if (t.sys < 0) return false;  // free tile of the arena
   P = a.params[t.sys];
   if (!P.active) return false;
   t.tl = warp - P.t_off;
@@ -217,7 +218,9 @@ __global__ void k_copyback(DevArrays a, int cur) {
   const double4_32a x = a.xtmp[t.s];
   a.x[cur][t.s] = x;
   a.xref[t.s] = x;
-  a.xq[cur][t.s] = fixed4(x, P.qscale);
+  const int4 q = fixed4(x, P.qscale);
+  a.xq[cur][t.s] = q;
+  a.xqref[t.s] = q;
   a.v[t.s] = a.vtmp[t.s];
   a.id[t.s] = a.idtmp[t.s];
   a.cell[t.s] = a.celltmp[t.s];
@@ -225,104 +228,231 @@ __global__ void k_copyback(DevArrays a, int cur) {
 
 // ----------------------------------------------- pair list (Sec. 2.1, Fig. 1)
 
-// Full list: every j != i with minimum-image r^2 < rl^2 (strict). Candidates
-// come from the 27 neighbour cells (or all particles when nc == 1). The decision
-// is the FP64 test ((dx dx + dy dy) + dz dz < rl^2, no fused operations). It is
-// taken first from the fixed-point separation in FP32, whose relative error on
-// r^2 is below 3.2e-6 for L <= 10^4 (quantisation <= 1 unit per axis, at least
-// 1.2e6 units per rl; five FP32 roundings): below rl^2 (1 - 1e-5) the pair is
-// certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only the thin
-// shell between needs the FP64 test. The result is identical to always taking it.
-__global__ void __launch_bounds__(kBlock) k_build_list(DevArrays a, int cur) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  const int lane = threadIdx.x & 31;
-  const double4_32a xi = a.x[cur][t.s];
-  const int4 qi = a.xq[cur][t.s];
-  const double4_32a* xs = a.x[cur] + P.p_off;
-  const int4* qs = a.xq[cur] + P.p_off;
-  uint32_t* out = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
-  const int kmax = P.kmax;
-  int count = 0;
+namespace {
 
-  auto test = [&](int j, unsigned code) {
-    const int4 qj = qs[j];
+// The FP64 membership test, exactly as the reference writes it: separation,
+// periodic image, (dx dx + dy dy) + dz dz < rl^2 without fused operations.
+// code = 0xff takes the minimum image d - L nearbyint(d / L) of each axis.
+// Returns the image code used, with bit 8 set if the pair is inside.
+__device__ __forceinline__ unsigned exact_inside(double xi, double yi, double zi, double xj, double yj, double zj,
+                                              unsigned code, double L, double rl2) {
+  const double d0 = __dsub_rn(xj, xi), d1 = __dsub_rn(yj, yi), d2 = __dsub_rn(zj, zi);
+  if (code == 0xffu) {
+    code = 0;
+    const double k0 = rint(__ddiv_rn(d0, L)), k1 = rint(__ddiv_rn(d1, L)), k2 = rint(__ddiv_rn(d2, L));
+    code |= k0 > 0.5 ? 2u : (k0 < -0.5 ? 1u : 0u);
+    code |= (k1 > 0.5 ? 2u : (k1 < -0.5 ? 1u : 0u)) << 2;
+    code |= (k2 > 0.5 ? 2u : (k2 < -0.5 ? 1u : 0u)) << 4;
+  }
+  const double dx = apply_image(d0, code & 3u, L);
+  const double dy = apply_image(d1, (code >> 2) & 3u, L);
+  const double dz = apply_image(d2, (code >> 4) & 3u, L);
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return code | (r2 < rl2 ? 0x100u : 0u);  // bit 8: inside
+}
+
+struct LBParams {
+  double L, rl2;
+  float rl2q_lo, rl2q_hi;
+  int n;
+};
+
+struct ListOut {
+  uint32_t* out;
+  int count;
+  int kmax;
+};
+
+// Test the candidates of slot range [lo, hi) (all with image `code`, or 0xff for
+// the per-pair minimum image) against particle li and append the partners.
+__device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const double4_32a* __restrict__ xs,
+                                            int lo, int hi, unsigned code, int li, const int4& qi,
+                                            const double4_32a& xi, const LBParams& P, ListOut& o) {
+  int4 qn = lo < hi ? qs[lo] : qi;
+  for (int j = lo; j < hi; ++j) {
+    const int4 qj = qn;
+    if (j + 1 < hi) qn = qs[j + 1];  // issue the next load before this test
     const float ax = (float)wrapped_diff(qj.x, qi.x);
     const float ay = (float)wrapped_diff(qj.y, qi.y);
     const float az = (float)wrapped_diff(qj.z, qi.z);
-    const float r2q = ax * ax + ay * ay + az * az;
-    if (!(r2q < P.rl2q_hi)) return;
-    bool inside = r2q < P.rl2q_lo;
-    if (!inside) {
+    const float r2q = fmaf(az, az, fmaf(ay, ay, ax * ax));
+    if (!(r2q < P.rl2q_hi) || j == li) continue;
+    unsigned cj = code;
+    bool inside = true;
+    if (!(r2q < P.rl2q_lo) || code == 0xffu) {
       const double4_32a xj = xs[j];
-      const double dx = apply_image(__dsub_rn(xj.x, xi.x), code & 3u, P.L);
-      const double dy = apply_image(__dsub_rn(xj.y, xi.y), (code >> 2) & 3u, P.L);
-      const double dz = apply_image(__dsub_rn(xj.z, xi.z), (code >> 4) & 3u, P.L);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      inside = r2 < P.rl2;
+      const unsigned r = exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, P.L, P.rl2);
+      cj = r & 0xffu;
+      inside = (r >> 8) & 1u;
     }
     if (inside) {
-      if (count < kmax) out[(int64_t)count * kTile] = (uint32_t)j | (code << kIdxBits);
-      ++count;
-    }
-  };
-
-  if (P.nc > 1) {
-    const int nc = P.nc;
-    const int ci = a.cell[t.s];
-    const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
-    const int32_t* cst = a.cstart + P.c_off;
-    for (int oz = -1; oz <= 1; ++oz) {
-      int nz = cz + oz;
-      unsigned shz = 0;
-      if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
-      for (int oy = -1; oy <= 1; ++oy) {
-        int ny = cy + oy;
-        unsigned shy = 0;
-        if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
-        for (int ox = -1; ox <= 1; ++ox) {
-          int nx = cx + ox;
-          unsigned shx = 0;
-          if (nx < 0) { nx += nc; shx = 2; } else if (nx >= nc) { nx -= nc; shx = 1; }
-          const int c = nx + nc * (ny + nc * nz);
-          const unsigned code = shx | (shy << 2) | (shz << 4);
-          const int lo = cst[c], hi = cst[c + 1];
-          for (int j = lo; j < hi; ++j)
-            if (j != t.local) test(j, code);
-        }
-      }
-    }
-  } else {
-    // every other particle; the image is the minimum image of the FP64 separation
-    for (int j = 0; j < P.n; ++j) {
-      if (j == t.local) continue;
-      const double4_32a xj = xs[j];
-      unsigned code = 0;
-      const double d[3] = {__dsub_rn(xj.x, xi.x), __dsub_rn(xj.y, xi.y), __dsub_rn(xj.z, xi.z)};
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        const double k = rint(__ddiv_rn(d[ax], P.L));
-        if (k > 0.5) code |= 2u << (2 * ax);
-        else if (k < -0.5) code |= 1u << (2 * ax);
-      }
-      test(j, code);
+      if (o.count < o.kmax) o.out[(int64_t)(o.count >> 2) * (4 * kTile) + (o.count & 3)] = (uint32_t)j | (cj << kIdxBits);
+      ++o.count;
     }
   }
-  a.ncnt[t.s] = count < kmax ? count : kmax;
-  if (count > kmax) atomicMax(&a.status[t.sys].overflow, count);
-  atomicMax(&a.status[t.sys].max_count, count);
+}
+
+}  // namespace
+
+// Full list: every j != i with minimum-image r^2 < rl^2 (strict); one thread per
+// particle, candidates from the 27 neighbour cells taken as 9 rows of 3 cells that
+// are contiguous in cell order (split in two where a row wraps), or from all
+// particles when nc == 1. Partners are appended in candidate order
+// (deterministic).
+//
+// The decision is the FP64 test ((dx dx + dy dy) + dz dz < rl^2, no fused
+// operations). It is taken first from the fixed-point separation in FP32, whose
+// relative error on r^2 is below 3.2e-6 for L <= 10^4 (quantisation <= 1 unit per
+// axis, at least 1.2e6 units per rl; five FP32 roundings): below rl^2 (1 - 1e-5)
+// the pair is certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only
+// the thin shell between needs the FP64 test. The result is identical to always
+// taking it.
+__global__ void __launch_bounds__(kBlock, 8) k_build_list(DevArrays a, int cur) {
+  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.ntiles) return;
+  const int sys = a.tile_sys[warp];
+  if (sys < 0 || !a.rebuild[sys]) return;
+  const SysParams* __restrict__ Pp = a.params + sys;
+  if (!Pp->active) return;
+  const int tl = warp - Pp->t_off;
+  const int li = tl * kTile + lane;
+  if (li >= Pp->n) return;
+  const int64_t p_off = Pp->p_off;
+  const double4_32a* xs = a.x[cur] + p_off;
+  const int4* qs = a.xq[cur] + p_off;
+  const double4_32a xi = xs[li];
+  const int4 qi = qs[li];
+  LBParams P{Pp->L, Pp->rl2, Pp->rl2q_lo, Pp->rl2q_hi, Pp->n};
+  ListOut o{a.nbr + list_word(Pp->l_off, tl, Pp->kmax, lane, 0), 0, Pp->kmax};
+  const int nc = Pp->nc;
+  const int32_t* cst = a.cstart + Pp->c_off;
+  int cx = 0, cy = 0, cz = 0;
+  if (nc > 1) {
+    const int ci = a.cell[p_off + li];
+    cx = ci % nc; cy = (ci / nc) % nc; cz = ci / (nc * nc);
+  }
+  // 9 rows of the 27-cell block (2 ranges each at most), or one range of all
+  // particles when nc == 1
+  const int nseg = nc > 1 ? 18 : 1;
+#pragma unroll 1
+  for (int seg = 0; seg < nseg; ++seg) {
+    int lo, hi;
+    unsigned code;
+    if (nc > 1) {
+      const int rowi = seg >> 1, part = seg & 1;
+      int nz = cz + rowi / 3 - 1, ny = cy + rowi % 3 - 1;
+      unsigned shz = 0, shy = 0;
+      if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
+      if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
+      const int row = nc * (ny + nc * nz);
+      code = (shy << 2) | (shz << 4);
+      // cells cx-1..cx+1 of this row: one contiguous range, or two where it wraps
+      if (cx == 0) {
+        if (part == 0) { lo = cst[row + nc - 1]; hi = cst[row + nc]; code |= 2u; }  // x image -L
+        else { lo = cst[row]; hi = cst[row + 2]; }
+      } else if (cx == nc - 1) {
+        if (part == 0) { lo = cst[row + nc - 2]; hi = cst[row + nc]; }
+        else { lo = cst[row]; hi = cst[row + 1]; code |= 1u; }                    // x image +L
+      } else {
+        if (part == 0) { lo = cst[row + cx - 1]; hi = cst[row + cx + 2]; }
+        else { lo = 0; hi = 0; }
+      }
+    } else {
+      lo = 0; hi = P.n; code = 0xffu;
+    }
+    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o);
+  }
+  a.ncnt[p_off + li] = o.count < o.kmax ? o.count : o.kmax;
+  if (o.count > o.kmax) atomicMax(&a.status[sys].overflow, o.count);
+  atomicMax(&a.status[sys].max_count, o.count);
 }
 
 // ------------------------------------- fused force + velocity-Verlet step
 
-// One launch: F at x[cur] from the list (or the stored F), then
-//   v += ka dt F   (completes the previous step),
-//   v += kb dt F   (first half-kick of the next step),
-//   x' = wrap(x + dt v) into x[cur ^ 1] (flags & kStepDrift),
-// and the largest squared displacement since the list build into disp2[sys].
+namespace {
+
+// Velocity-Verlet update of one particle after its force F is known:
+//   v += ka dt F (completes the previous step), v += kb dt F (first half-kick of
+//   the next step; kept as two roundings so that a run split over several calls
+//   equals one uninterrupted call bit for bit), then optionally the drift
+//   x' = x + dt v into x[cur ^ 1] (not wrapped: list images stay valid) and the
+//   squared displacement since the list build for the validity check.
 template <bool kFP32>
-__global__ void __launch_bounds__(kBlock) k_step(DevArrays a, int cur, double ka, double kb, int flags) {
+__device__ __forceinline__ unsigned long long integrate(const DevArrays& a, const SysParams& P, const TileCtx& t,
+                                                        int cur, const double4_32a& xi, double Fx, double Fy,
+                                                        double Fz, double ka, double kb, int flags) {
+  if (flags & kStepStoreF) a.f[t.s] = make_double4_32a(Fx, Fy, Fz, 0.0);
+  double4_32a v = a.v[t.s];
+  const double dt = P.dt;
+  if (ka != 0.0) { const double h = ka * dt; v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
+  if (kb != 0.0) { const double h = kb * dt; v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
+  a.v[t.s] = v;
+  if (!(flags & kStepDrift)) return 0ull;
+  double4_32a xn;
+  xn.x = fma(dt, v.x, xi.x);
+  xn.y = fma(dt, v.y, xi.y);
+  xn.z = fma(dt, v.z, xi.z);
+  xn.w = 0.0;
+  a.x[cur ^ 1][t.s] = xn;
+  if (!(finite_bits(xn.x) && finite_bits(xn.y) && finite_bits(xn.z) && finite_bits(v.x) &&
+        finite_bits(v.y) && finite_bits(v.z))) {
+    a.status[t.sys].nonfinite = 1;
+    return ~0ull;
+  }
+  if (kFP32) {
+    // check in fixed point: exact integer squared displacement of the shadow
+    const int4 q = fixed4(xn, P.qscale);
+    a.xq[cur ^ 1][t.s] = q;
+    const int4 r = a.xqref[t.s];
+    const long long ex = wrapped_diff(q.x, r.x), ey = wrapped_diff(q.y, r.y), ez = wrapped_diff(q.z, r.z);
+    return (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey) + (unsigned long long)(ez * ez);
+  }
+  // exact FP64 check, the same operations as the reference
+  const double4_32a r = a.xref[t.s];
+  const double ex = __dsub_rn(xn.x, r.x), ey = __dsub_rn(xn.y, r.y), ez = __dsub_rn(xn.z, r.z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return (unsigned long long)__double_as_longlong(d2);
+}
+
+__device__ __forceinline__ void warp_max_disp(const DevArrays& a, int sys, unsigned long long d2b, int flags) {
+  if (!(flags & kStepDrift)) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(kFull, d2b, o);
+    d2b = y > d2b ? y : d2b;
+  }
+  if ((threadIdx.x & 31) == 0 && d2b) atomicMax(&a.disp2[sys], d2b);
+}
+
+// FP32 pair force from an exact fixed-point separation; returns 0 for invalid
+// slots and for r >= rc without branching (g (24 r^-8 - 48 r^-14 + 8 c2)).
+__device__ __forceinline__ void pair_fp32(const int4& qi, const int4& qj, bool valid, float qu, float rc2,
+                                          float c2x8, float& fx, float& fy, float& fz) {
+  const float dx = (float)wrapped_diff(qj.x, qi.x) * qu;
+  const float dy = (float)wrapped_diff(qj.y, qi.y) * qu;
+  const float dz = (float)wrapped_diff(qj.z, qi.z) * qu;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  const bool in = valid && r2 < rc2;
+  const float r2s = in ? r2 : 1.0f;
+  float ir2;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ir2) : "f"(r2s));
+  ir2 = ir2 * fmaf(-r2s, ir2, 2.0f);  // one Newton step
+  const float ir6 = ir2 * ir2 * ir2;
+  float g = fmaf(ir2 * ir6, fmaf(-48.0f, ir6, 24.0f), c2x8);
+  g = in ? g : 0.0f;
+  fx = fmaf(g, dx, fx);
+  fy = fmaf(g, dy, fy);
+  fz = fmaf(g, dz, fz);
+}
+
+}  // namespace
+
+// FP32-force form: pair arithmetic in FP32 from fixed-point separations (the
+// wrapped integer difference is already the minimum image), four partners per
+// 16-byte list load, the next group's load issued before the current group's
+// gathers are used (software pipelining, the role of Algorithm 1's unrolling).
+__global__ void __launch_bounds__(kBlock) k_step_fp32(DevArrays a, int cur, double ka, double kb, int flags) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
@@ -337,103 +467,84 @@ __global__ void __launch_bounds__(kBlock) k_step(DevArrays a, int cur, double ka
     }
   } else if (t.act) {
     const int cnt = a.ncnt[t.s];
-    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
-    if (kFP32) {
-      // Pair arithmetic in FP32 from exact fixed-point separations (the integer
-      // difference of the shadow coordinates is already the minimum image).
-      const int4* qs = a.xq[cur] + P.p_off;
-      const int4 qi = a.xq[cur][t.s];
-      const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
-      float fx = 0.f, fy = 0.f, fz = 0.f;
-      for (int k = 0; k < cnt; ++k) {
-        const uint32_t e = __ldg(lp + (int64_t)k * kTile);
-        const int4 qj = qs[e & kIdxMask];
-        const float dx = (float)wrapped_diff(qj.x, qi.x) * qu;
-        const float dy = (float)wrapped_diff(qj.y, qi.y) * qu;
-        const float dz = (float)wrapped_diff(qj.z, qi.z) * qu;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < rc2) {
-          const float ir2 = __frcp_rn(r2);
-          const float ir6 = ir2 * ir2 * ir2;
-          const float g = ir2 * ir6 * (24.0f - 48.0f * ir6) + c2x8;
-          fx = fmaf(g, dx, fx);
-          fy = fmaf(g, dy, fy);
-          fz = fmaf(g, dz, fz);
-        }
+    const uint4* lp4 = (const uint4*)(a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0));
+    const int4* qs = a.xq[cur] + P.p_off;
+    const int4 qi = a.xq[cur][t.s];
+    const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
+    const uint32_t self = (uint32_t)t.local;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const int ng = (cnt + 3) >> 2;
+    uint4 e = ng > 0 ? __ldg(lp4) : make_uint4(self, self, self, self);
+    for (int g = 0; g < ng; ++g) {
+      const uint4 en = (g + 1 < ng) ? __ldg(lp4 + (int64_t)(g + 1) * kTile) : e;
+      const int rem = cnt - 4 * g;
+      const uint32_t j0 = e.x & kIdxMask;
+      const uint32_t j1 = rem > 1 ? (e.y & kIdxMask) : self;
+      const uint32_t j2 = rem > 2 ? (e.z & kIdxMask) : self;
+      const uint32_t j3 = rem > 3 ? (e.w & kIdxMask) : self;
+      const int4 q0 = qs[j0], q1 = qs[j1], q2 = qs[j2], q3 = qs[j3];
+      pair_fp32(qi, q0, true, qu, rc2, c2x8, fx, fy, fz);
+      pair_fp32(qi, q1, rem > 1, qu, rc2, c2x8, fx, fy, fz);
+      pair_fp32(qi, q2, rem > 2, qu, rc2, c2x8, fx, fy, fz);
+      pair_fp32(qi, q3, rem > 3, qu, rc2, c2x8, fx, fy, fz);
+      e = en;
+    }
+    Fx = fx; Fy = fy; Fz = fz;
+  }
+  unsigned long long d2b = 0ull;
+  if (t.act) d2b = integrate<true>(a, P, t, cur, xi, Fx, Fy, Fz, ka, kb, flags);
+  warp_max_disp(a, t.sys, d2b, flags);
+}
+
+// FP64 form. The FP64 pipe is the bound: per listed pair 3 DADD + 3 (r^2); per
+// pair inside rc the reciprocal (3 DFMA after an integer-built FP32 seed),
+// powers (3), factor (2) and accumulation (3). The cutoff test compares bit
+// patterns (r^2 >= 0), so it costs no FP64 instruction.
+__global__ void __launch_bounds__(kBlock) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P)) return;
+  const int lane = threadIdx.x & 31;
+  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+  if (t.act) xi = a.x[cur][t.s];
+  if (flags & kStepUseStoredF) {
+    if (t.act) {
+      const double4_32a f = a.f[t.s];
+      Fx = f.x; Fy = f.y; Fz = f.z;
+    }
+  } else if (t.act) {
+    const int cnt = a.ncnt[t.s];
+    const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    const long long rc2b = __double_as_longlong(P.rc2);
+    const double c2x8 = 8.0 * P.c2, L = P.L;
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
+      const double4_32a xj = xs[e & kIdxMask];
+      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+      const unsigned code = e >> kIdxBits;
+      if (code) {
+        dx = apply_image(dx, code & 3u, L);
+        dy = apply_image(dy, (code >> 2) & 3u, L);
+        dz = apply_image(dz, (code >> 4) & 3u, L);
       }
-      Fx = fx; Fy = fy; Fz = fz;
-    } else {
-      const double4_32a* xs = a.x[cur] + P.p_off;
-      const long long rc2b = __double_as_longlong(P.rc2);
-      const double c2x8 = 8.0 * P.c2, L = P.L;
-      for (int k = 0; k < cnt; ++k) {
-        const uint32_t e = __ldg(lp + (int64_t)k * kTile);
-        const double4_32a xj = xs[e & kIdxMask];
-        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-        const unsigned code = e >> kIdxBits;
-        if (code) {
-          dx = apply_image(dx, code & 3u, L);
-          dy = apply_image(dy, (code >> 2) & 3u, L);
-          dz = apply_image(dz, (code >> 4) & 3u, L);
-        }
-        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        if (__double_as_longlong(r2) < rc2b) {  // r2 >= 0: integer order = value order
-          const double ir2 = rcp_f64(r2);
-          const double ir4 = ir2 * ir2;
-          const double ir6 = ir4 * ir2;
-          const double ir8 = ir4 * ir4;
-          const double g = fma(ir8, fma(-48.0, ir6, 24.0), c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
-          Fx = fma(g, dx, Fx);
-          Fy = fma(g, dy, Fy);
-          Fz = fma(g, dz, Fz);
-        }
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      if (__double_as_longlong(r2) < rc2b) {
+        const double ir2 = rcp_f64(r2);
+        const double ir4 = ir2 * ir2;
+        const double ir6 = ir4 * ir2;
+        const double ir8 = ir4 * ir4;
+        const double g = fma(ir8, fma(-48.0, ir6, 24.0), c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+        Fx = fma(g, dx, Fx);
+        Fy = fma(g, dy, Fy);
+        Fz = fma(g, dz, Fz);
       }
     }
   }
   unsigned long long d2b = 0ull;
-  if (t.act) {
-    if (flags & kStepStoreF) a.f[t.s] = make_double4_32a(Fx, Fy, Fz, 0.0);
-    double4_32a v = a.v[t.s];
-    const double dt = P.dt;
-    if (ka != 0.0) {
-      const double h = ka * dt;
-      v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z);
-    }
-    if (kb != 0.0) {
-      const double h = kb * dt;
-      v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z);
-    }
-    a.v[t.s] = v;
-    if (flags & kStepDrift) {
-      // no wrap here: images in the list assume unwrapped motion since the build
-      double4_32a xn;
-      xn.x = fma(dt, v.x, xi.x);
-      xn.y = fma(dt, v.y, xi.y);
-      xn.z = fma(dt, v.z, xi.z);
-      xn.w = 0.0;
-      a.x[cur ^ 1][t.s] = xn;
-      if (kFP32) a.xq[cur ^ 1][t.s] = fixed4(xn, P.qscale);
-      if (!(finite_bits(xn.x) && finite_bits(xn.y) && finite_bits(xn.z) && finite_bits(v.x) &&
-            finite_bits(v.y) && finite_bits(v.z)))
-        a.status[t.sys].nonfinite = 1;
-      // displacement since the list build (positions are not wrapped in between)
-      const double4_32a r = a.xref[t.s];
-      const double ex = __dsub_rn(xn.x, r.x);
-      const double ey = __dsub_rn(xn.y, r.y);
-      const double ez = __dsub_rn(xn.z, r.z);
-      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-      d2b = (unsigned long long)__double_as_longlong(d2);
-      if (!finite_bits(d2)) d2b = 0x7ff0000000000000ull;
-    }
-  }
-  if (flags & kStepDrift) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long y = __shfl_xor_sync(kFull, d2b, o);
-      d2b = y > d2b ? y : d2b;
-    }
-    if (lane == 0 && d2b) atomicMax(&a.disp2[t.sys], d2b);
-  }
+  if (t.act) d2b = integrate<false>(a, P, t, cur, xi, Fx, Fy, Fz, ka, kb, flags);
+  warp_max_disp(a, t.sys, d2b, flags);
 }
 
 // ------------------------------------------------- observables (FP64 sums)
@@ -451,9 +562,9 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur) {
     const double4_32a xi = a.x[cur][t.s];
     const double4_32a* xs = a.x[cur] + P.p_off;
     const int cnt = a.ncnt[t.s];
-    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+    const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = lp[(int64_t)k * kTile];
+      const uint32_t e = lp[(int64_t)(k >> 2) * (4 * kTile) + (k & 3)];
       const double4_32a xj = xs[e & kIdxMask];
       const unsigned code = e >> kIdxBits;
       const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
@@ -497,10 +608,10 @@ __global__ void __launch_bounds__(kBlock) k_pair_stats(DevArrays a, int cur, uns
     const double4_32a xi = a.x[cur][t.s];
     const double4_32a* xs = a.x[cur] + P.p_off;
     const int cnt = a.ncnt[t.s];
-    const uint32_t* lp = a.nbr + P.l_off + (int64_t)t.tl * P.kmax * kTile + lane;
+    const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
     listed = (unsigned)cnt;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = lp[(int64_t)k * kTile];
+      const uint32_t e = lp[(int64_t)(k >> 2) * (4 * kTile) + (k & 3)];
       const double4_32a xj = xs[e & kIdxMask];
       const unsigned code = e >> kIdxBits;
       const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
@@ -589,10 +700,10 @@ void launch_build_list(const DevArrays& a, int cur, cudaStream_t s) {
   k_build_list<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
-  k_step<false><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+  k_step_fp64<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
 }
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
-  k_step<true><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+  k_step_fp32<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
 }
 void launch_pe_virial(const DevArrays& a, int cur, cudaStream_t s) {
   k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);

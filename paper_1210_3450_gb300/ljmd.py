@@ -62,6 +62,26 @@ SIGNATURES = {
     "md_get_timing": (C.c_int, [_P, _PD]),
     "md_forces_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, _P, _P]),
     "md_destroy": (None, [_P]),
+    "md_batch_create": (C.c_int, [C.c_int, _P, C.c_int, C.POINTER(_P)]),
+    "md_batch_create_arena": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.POINTER(_P)]),
+    "md_batch_footprint": (C.c_int, [_P, _PI64, _PI64, _PI64]),
+    "md_batch_add": (C.c_int, [_P, _P, C.POINTER(C.c_int)]),
+    "md_batch_remove": (C.c_int, [_P, C.c_int]),
+    "md_batch_usage": (C.c_int, [_P, _PI64]),
+    "md_batch_set_active": (C.c_int, [_P, C.c_int, C.c_int]),
+    "md_batch_set_precision": (C.c_int, [_P, C.c_int]),
+    "md_batch_set_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
+    "md_batch_set_state_dev": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "md_batch_get_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
+    "md_batch_get_state_dev": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "md_batch_step": (C.c_int, [_P, C.c_int64, _PD]),
+    "md_batch_step_async": (C.c_int, [_P, C.c_int64, _PD, _P]),
+    "md_batch_forces": (C.c_int, [_P, C.c_int, _PD]),
+    "md_batch_observables": (C.c_int, [_P, _PD]),
+    "md_batch_stats": (C.c_int, [_P, C.c_int, _PI64, _PI64]),
+    "md_batch_set_timing": (C.c_int, [_P, C.c_int]),
+    "md_batch_get_timing": (C.c_int, [_P, _PD]),
+    "md_batch_destroy": (None, [_P]),
     "md_last_error": (C.c_char_p, []),
     "md_version": (C.c_char_p, []),
 }
@@ -234,6 +254,156 @@ class LJSystem:
         partners = np.empty(max(total, 1), dtype=np.int32)
         _check(_lib.md_get_list(self._h, start.ctypes.data_as(_PI64), partners.ctypes.data_as(_PI32)))
         return start, partners[:total]
+
+
+class SysDesc(C.Structure):
+    """md_sys_desc: one system of a batch."""
+    _fields_ = [("N", C.c_int64), ("box_L", C.c_double), ("rc", C.c_double), ("skin", C.c_double)]
+
+
+def footprint(n: int, box: float, rc: float, skin: float) -> dict:
+    """Arena space one system needs (md_batch_footprint)."""
+    d = SysDesc(int(n), float(box), float(rc), float(skin))
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load_library().md_batch_footprint(C.byref(d), C.byref(a), C.byref(b), C.byref(c)))
+    return dict(slots=a.value, cells=b.value, list_words=c.value)
+
+
+class LJBatch:
+    """Many independent LJ systems in one device arena (md_batch_*). Either a
+    fixed set (``systems=[(n, box, rc, skin), ...]``, ids 0..k-1) or an empty
+    arena with capacities (``arena=dict(slots=, cells=, list_words=, max_systems=)``)
+    that systems are added to and removed from."""
+
+    def __init__(self, systems=None, arena=None, precision: int = MD_FP64):
+        lib = load_library()
+        h = _P()
+        if systems is not None:
+            descs = (SysDesc * len(systems))(*[SysDesc(int(n), float(b), float(rc), float(sk))
+                                               for (n, b, rc, sk) in systems])
+            _check(lib.md_batch_create(len(systems), C.cast(descs, _P), int(precision), C.byref(h)))
+            self.max_systems = len(systems)
+            self._n = {k: int(systems[k][0]) for k in range(len(systems))}
+        else:
+            a = arena
+            _check(lib.md_batch_create_arena(int(a["slots"]), int(a["cells"]), int(a["list_words"]),
+                                             int(a["max_systems"]), int(precision), C.byref(h)))
+            self.max_systems = int(a["max_systems"])
+            self._n = {}
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.md_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, n: int, box: float, rc: float, skin: float) -> int:
+        d = SysDesc(int(n), float(box), float(rc), float(skin))
+        i = C.c_int()
+        _check(_lib.md_batch_add(self._h, C.byref(d), C.byref(i)))
+        self._n[i.value] = int(n)
+        return i.value
+
+    def try_add(self, n: int, box: float, rc: float, skin: float):
+        """add(), or None when the arena has no room (MD_ERR_OOM)."""
+        try:
+            return self.add(n, box, rc, skin)
+        except MDError as e:
+            if e.code == MD_ERR_OOM:
+                return None
+            raise
+
+    def remove(self, sid: int):
+        _check(_lib.md_batch_remove(self._h, int(sid)))
+        self._n.pop(sid, None)
+
+    def usage(self) -> dict:
+        o = np.zeros(8, dtype=np.int64)
+        _check(_lib.md_batch_usage(self._h, o.ctypes.data_as(_PI64)))
+        keys = ["slots", "slots_free", "cells", "cells_free", "list_words", "list_words_free",
+                "systems", "systems_used"]
+        return dict(zip(keys, [int(v) for v in o]))
+
+    def set_active(self, sid: int, on: bool):
+        _check(_lib.md_batch_set_active(self._h, int(sid), 1 if on else 0))
+
+    def set_precision(self, mode: int):
+        _check(_lib.md_batch_set_precision(self._h, int(mode)))
+
+    def set_state(self, sid: int, x, v):
+        n = self._n[sid]
+        x = _host3(x, n)
+        v = _host3(v, n)
+        _check(_lib.md_batch_set_state(self._h, int(sid), _pd(x), _pd(v)))
+
+    def set_state_dev(self, sid: int, x, v, stream=None):
+        n = self._n[sid]
+        _check(_lib.md_batch_set_state_dev(self._h, int(sid), _dev_ptr(x, n), _dev_ptr(v, n),
+                                           _stream_ptr(stream)))
+
+    def get_state(self, sid: int):
+        n = self._n[sid]
+        x = np.empty((n, 3))
+        v = np.empty((n, 3))
+        _check(_lib.md_batch_get_state(self._h, int(sid), _pd(x), _pd(v)))
+        return x, v
+
+    def _dt(self, dt):
+        arr = np.zeros(self.max_systems)
+        if np.isscalar(dt):
+            arr[:] = float(dt)
+        elif isinstance(dt, dict):
+            for k, val in dt.items():
+                arr[k] = val
+        else:
+            arr[:len(dt)] = dt
+        return arr
+
+    def step(self, nsteps: int, dt):
+        arr = self._dt(dt)
+        _check(_lib.md_batch_step(self._h, int(nsteps), _pd(arr)))
+
+    def step_async(self, nsteps: int, dt, stream=None):
+        arr = self._dt(dt)
+        _check(_lib.md_batch_step_async(self._h, int(nsteps), _pd(arr), _stream_ptr(stream)))
+
+    def forces(self, sid: int) -> np.ndarray:
+        f = np.empty((self._n[sid], 3))
+        _check(_lib.md_batch_forces(self._h, int(sid), _pd(f)))
+        return f
+
+    def observables(self) -> np.ndarray:
+        """(max_systems, 5): pe, virial, ke, T, P per id."""
+        out = np.zeros((self.max_systems, 5))
+        _check(_lib.md_batch_observables(self._h, _pd(out)))
+        return out
+
+    def stats(self, sid: int) -> dict:
+        r, s = C.c_int64(), C.c_int64()
+        _check(_lib.md_batch_stats(self._h, int(sid), C.byref(r), C.byref(s)))
+        return dict(rebuilds=r.value, steps=s.value)
+
+    def set_timing(self, on: bool = True):
+        _check(_lib.md_batch_set_timing(self._h, 1 if on else 0))
+
+    def get_timing(self) -> dict:
+        out = np.zeros(8)
+        _check(_lib.md_batch_get_timing(self._h, _pd(out)))
+        return dict(step_ms=out[0], step_launches=int(out[1]), list_ms=out[2],
+                    list_launches=int(out[3]), bin_ms=out[4], rebuilds=int(out[5]),
+                    launches=int(out[6]))
 
 
 def forces_noalloc(x, box: float, rc: float, f, stream=None):

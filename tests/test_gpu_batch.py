@@ -1,0 +1,137 @@
+"""Batched replicas and the continuous-batching arena (md_batch_*).
+
+Bar: every system's state, rebuild count and observables after a batched run are
+bit-for-bit those of the same system run alone (the kernels do no cross-system
+arithmetic and every per-system reduction has a fixed order), in both precision
+modes; systems added to and removed from a running arena keep that property.
+"""
+import numpy as np
+import pytest
+
+import lj_inputs as li
+
+pytestmark = pytest.mark.gpu
+
+
+def _systems():
+    out = []
+    x, box = li.perturbed_fcc(4000, 0.8442, 0.08, 301)
+    out.append(dict(x=x, v=li.maxwell_boltzmann(4000, 0.722, 302), box=box, rc=2.5, skin=0.3, dt=0.005))
+    x, box = li.perturbed_fcc(500, 0.85, 0.05, 303)          # fewer than 3 cells: all pairs
+    out.append(dict(x=x, v=li.maxwell_boltzmann(500, 1.2, 304), box=box, rc=2.5, skin=0.3, dt=0.004))
+    x, box = li.perturbed_fcc(1999, 0.60, 0.1, 305)          # ragged tile
+    out.append(dict(x=x, v=li.maxwell_boltzmann(1999, 1.0, 306), box=box, rc=2.5, skin=0.3, dt=0.005))
+    x, box = li.perturbed_fcc(2916, 0.70, 0.1, 307)           # rc = 3.0
+    out.append(dict(x=x, v=li.maxwell_boltzmann(2916, 0.9, 308), box=box, rc=3.0, skin=0.3, dt=0.005))
+    x, box = li.perturbed_fcc(33, 0.1, 0.2, 309)
+    out.append(dict(x=x, v=li.maxwell_boltzmann(33, 0.8, 310), box=box, rc=2.5, skin=0.3, dt=0.003))
+    return out
+
+
+def _alone(ljmd, s, nsteps, precision):
+    with ljmd.LJSystem(s["box"], len(s["x"]), s["rc"], s["skin"], precision) as m:
+        m.set_state(s["x"], s["v"])
+        m.step(nsteps, s["dt"])
+        x, v = m.get_state()
+        return x, v, m.stats()["rebuilds"], m.observables()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32"])
+def test_batch_equals_alone_bitwise(ljmd, precision):
+    syss = _systems()
+    nsteps = 60
+    ref = [_alone(ljmd, s, nsteps, precision) for s in syss]
+    with ljmd.LJBatch(systems=[(len(s["x"]), s["box"], s["rc"], s["skin"]) for s in syss],
+                      precision=precision) as b:
+        for k, s in enumerate(syss):
+            b.set_state(k, s["x"], s["v"])
+        b.step(nsteps, [s["dt"] for s in syss])
+        obs = b.observables()
+        for k in range(len(syss)):
+            x, v = b.get_state(k)
+            np.testing.assert_array_equal(x, ref[k][0])
+            np.testing.assert_array_equal(v, ref[k][1])
+            assert b.stats(k)["rebuilds"] == ref[k][2]
+            o = ref[k][3]
+            np.testing.assert_array_equal(obs[k], [o["pe"], o["virial"], o["ke"], o["temperature"], o["pressure"]])
+
+
+def test_batch_forces_match_oracle(ljmd, oracle):
+    syss = _systems()
+    with ljmd.LJBatch(systems=[(len(s["x"]), s["box"], s["rc"], s["skin"]) for s in syss]) as b:
+        for k, s in enumerate(syss):
+            b.set_state(k, s["x"], s["v"])
+        for k, s in enumerate(syss):
+            f = b.forces(k)
+            ref = oracle.forces_brute(s["x"], s["box"], s["rc"])
+            rms = np.sqrt((ref ** 2).sum(1).mean())
+            assert np.abs(f - ref).max() / rms <= 1e-12
+
+
+def test_arena_add_remove_keeps_results(ljmd):
+    """Continuous batching: B runs throughout; A leaves after 30 steps and C takes
+    its place; B and C end bit-for-bit equal to their runs alone."""
+    syss = _systems()
+    A, B, C = syss[0], syss[2], syss[3]
+    fps = [ljmd.footprint(len(s["x"]), s["box"], s["rc"], s["skin"]) for s in (A, B, C)]
+    arena = dict(slots=sum(f["slots"] for f in fps[:2]) + 64,
+                 cells=sum(f["cells"] for f in fps) + 16,
+                 list_words=sum(f["list_words"] for f in fps[:2]) + fps[2]["list_words"] + 4096,
+                 max_systems=4)
+    for precision in (0, 1):
+        with ljmd.LJBatch(arena=arena, precision=precision) as b:
+            ia = b.add(len(A["x"]), A["box"], A["rc"], A["skin"])
+            ib = b.add(len(B["x"]), B["box"], B["rc"], B["skin"])
+            b.set_state(ia, A["x"], A["v"])
+            b.set_state(ib, B["x"], B["v"])
+            b.step(30, {ia: A["dt"], ib: B["dt"]})
+            # C does not fit while A is there
+            assert b.try_add(len(C["x"]), C["box"], C["rc"], C["skin"]) is None
+            b.remove(ia)
+            ic = b.add(len(C["x"]), C["box"], C["rc"], C["skin"])
+            b.set_state(ic, C["x"], C["v"])
+            b.step(30, {ib: B["dt"], ic: C["dt"]})
+            xb, vb = b.get_state(ib)
+            xc, vc = b.get_state(ic)
+            u = b.usage()
+            assert u["systems_used"] == 2
+        rb = _alone(ljmd, B, 60, precision)
+        rc_ = _alone(ljmd, C, 30, precision)
+        np.testing.assert_array_equal(xb, rb[0])
+        np.testing.assert_array_equal(vb, rb[1])
+        np.testing.assert_array_equal(xc, rc_[0])
+        np.testing.assert_array_equal(vc, rc_[1])
+
+
+def test_inactive_system_is_frozen(ljmd):
+    syss = _systems()[:2]
+    with ljmd.LJBatch(systems=[(len(s["x"]), s["box"], s["rc"], s["skin"]) for s in syss]) as b:
+        for k, s in enumerate(syss):
+            b.set_state(k, s["x"], s["v"])
+        x0, v0 = b.get_state(1)
+        b.set_active(1, False)
+        b.step(10, [s["dt"] for s in syss])
+        x1, v1 = b.get_state(1)
+        np.testing.assert_array_equal(x0, x1)
+        np.testing.assert_array_equal(v0, v1)
+        assert b.stats(0)["steps"] == 10 and b.stats(1)["steps"] == 0
+
+
+def test_replica_workload_sample_matches_alone(ljmd):
+    """32 systems drawn like the 256-replica workload (N log-uniform in
+    [500, 32000], rho in [0.60, 0.85], T in [0.7, 1.2]) in FP32-force mode:
+    each equals its run alone after 40 steps."""
+    syss = li.batch_systems(count=32, seed=1004)
+    with ljmd.LJBatch(systems=[(c.n, c.box, c.rc, c.skin) for c in syss], precision=1) as b:
+        for k, c in enumerate(syss):
+            b.set_state(k, c.x, c.v)
+        b.step(40, [c.dt for c in syss])
+        for k in [0, 7, 13, 31]:
+            c = syss[k]
+            x, v = b.get_state(k)
+            with ljmd.LJSystem(c.box, c.n, c.rc, c.skin, 1) as m:
+                m.set_state(c.x, c.v)
+                m.step(40, c.dt)
+                xr, vr = m.get_state()
+            np.testing.assert_array_equal(x, xr)
+            np.testing.assert_array_equal(v, vr)
