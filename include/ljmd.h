@@ -111,6 +111,13 @@ MD_API int md_forces_dev(md_ctx* ctx, double* f_dev, void* stream);
  * Sums are accumulated in FP64 in a fixed order (deterministic). */
 MD_API int md_observables(md_ctx* ctx, double* pe, double* virial, double* ke, double* T, double* P);
 
+/* Kinetic energy sum_i |v_i|^2 / 2 only (no pair sums; cheaper than md_observables). */
+MD_API int md_kinetic_energy(md_ctx* ctx, double* ke);
+
+/* v_i *= factor for every particle (e.g. a velocity-rescaling thermostat between
+ * md_step calls). Positions, list and forces stay valid. */
+MD_API int md_scale_velocities(md_ctx* ctx, double factor);
+
 /* Counters: list builds since md_create (including forced ones) and steps taken. */
 MD_API int md_stats(md_ctx* ctx, int64_t* rebuilds, int64_t* steps);
 
@@ -165,6 +172,18 @@ MD_API int md_get_timing(md_ctx* ctx, double* out8);
  * and must be serialised by the caller. Errors: MD_ERR_ARG, MD_ERR_CUDA. */
 MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, double rc,
                              double* f_dev, void* stream);
+
+/* Launch shapes of the hot kernels (results do not depend on them, only speed):
+ *   MD_TUNE_STEP_BLOCK   threads per block of the force + integration kernel: 64, 128, 256
+ *   MD_TUNE_STEP_GROUPS  FP32-force partners loaded per iteration, in groups of 4: 1, 2
+ *   MD_TUNE_LIST_BLOCK   threads per block of the pair-list build: 64, 128, 256
+ * Defaults 128 / 2 / 128. The autotuner (paper_1210_3450_gb300.autotune) times the
+ * choices on the caller's own systems and sets the fastest. */
+#define MD_TUNE_STEP_BLOCK 0
+#define MD_TUNE_STEP_GROUPS 1
+#define MD_TUNE_LIST_BLOCK 2
+MD_API int md_set_tuning(md_ctx* ctx, int key, int value);
+MD_API int md_get_tuning(md_ctx* ctx, int key, int* value);
 
 /* Release all resources of ctx (NULL is ignored). */
 MD_API void md_destroy(md_ctx* ctx);
@@ -238,7 +257,15 @@ MD_API int md_batch_forces(md_batch* b, int id, double* f);
  * (as md_observables); out holds 5 * max_systems doubles (inactive ids get zeros). */
 MD_API int md_batch_observables(md_batch* b, double* out);
 
+/* Kinetic energy of every active system: ke[id] (max_systems doubles, 0 if inactive). */
+MD_API int md_batch_kinetic_energy(md_batch* b, double* ke);
+
+/* v *= factor[id] for every active system (factor: max_systems doubles). */
+MD_API int md_batch_scale_velocities(md_batch* b, const double* factor);
+
 MD_API int md_batch_stats(md_batch* b, int id, int64_t* rebuilds, int64_t* steps);
+MD_API int md_batch_set_tuning(md_batch* b, int key, int value);
+MD_API int md_batch_get_tuning(md_batch* b, int key, int* value);
 MD_API int md_batch_set_timing(md_batch* b, int on);
 MD_API int md_batch_get_timing(md_batch* b, double* out8);
 MD_API void md_batch_destroy(md_batch* b);

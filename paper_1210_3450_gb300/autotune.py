@@ -1,0 +1,87 @@
+"""Autotuner of the kernels' launch shapes.
+
+Times every choice of (step-kernel threads per block, FP32 partner groups per
+iteration) and of list-build threads per block on the caller's own system or
+batch, with the library's CUDA-event timing, and sets the fastest. Results are
+kept in a JSON cache keyed by the workload's shape (precision, particles rounded
+to a power of two, density to 0.05, number of systems), so a later run of the
+same shape reuses them without timing.
+
+    from paper_1210_3450_gb300 import autotune
+    best = autotune.tune(system, dt=0.005)          # LJSystem or LJBatch with a state
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
+
+STEP_BLOCKS = (64, 128, 256)
+STEP_GROUPS = (1, 2)
+LIST_BLOCKS = (64, 128, 256)
+
+
+def shape_key(precision: int, particles: int, density: float, systems: int) -> str:
+    return (f"p{precision}-n{2 ** round(math.log2(max(particles, 1)))}-"
+            f"rho{round(density * 20) / 20:.2f}-s{systems}")
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None = DEFAULT_CACHE,
+         fp32: bool = True) -> dict:
+    """Time the launch shapes on `system` (it advances by the timed steps) and set
+    the fastest. With a cache file and a key already in it, set that instead."""
+    if cache and key:
+        known = _load(cache).get(key)
+        if known:
+            system.set_tuning(**known["tuning"])
+            return known
+    step_choices = list(itertools.product(STEP_BLOCKS, STEP_GROUPS if fp32 else (1,)))
+    results = {}
+    system.step(5, dt)
+    for blk, grp in step_choices:
+        system.set_tuning(step_block=blk, step_groups=grp)
+        system.step(2, dt)
+        system.set_timing(True)
+        system.step(steps, dt)
+        t = system.get_timing()
+        results[f"step{blk}x{grp}"] = t["step_ms"] / max(t["step_launches"], 1)
+    blk, grp = min(step_choices, key=lambda c: results[f"step{c[0]}x{c[1]}"])
+    system.set_tuning(step_block=blk, step_groups=grp)
+    list_times = {}
+    for lb in LIST_BLOCKS:
+        system.set_tuning(list_block=lb)
+        system.set_timing(True)
+        system.build_list() if hasattr(system, "build_list") else None
+        system.step(steps, dt)
+        t = system.get_timing()
+        if t["list_launches"]:
+            list_times[lb] = t["list_ms"] / t["list_launches"]
+    lbest = min(list_times, key=list_times.get) if list_times else 128
+    system.set_tuning(list_block=lbest)
+    out = dict(tuning=dict(step_block=blk, step_groups=grp, list_block=lbest),
+               step_ms=results, list_ms={str(k): v for k, v in list_times.items()})
+    if cache and key:
+        data = _load(cache)
+        data[key] = out
+        _save(cache, data)
+    return out

@@ -180,6 +180,26 @@ int md_observables(md_ctx* c, double* pe, double* virial, double* ke, double* T,
   return MD_OK;
 }
 
+int md_kinetic_energy(md_ctx* c, double* ke) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!ke) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  double o[3];
+  if ((r = c->eng.observables(o, c->stream, false))) return r;
+  *ke = o[2];
+  return MD_OK;
+}
+
+int md_scale_velocities(md_ctx* c, double factor) {
+  int r = check_ctx(c);
+  if (r) return r;
+  std::vector<double> f{factor};
+  return c->eng.scale_velocities(f, c->stream);
+}
+
 int md_stats(md_ctx* c, int64_t* rebuilds, int64_t* steps) {
   int r = check_ctx(c);
   if (r) return r;
@@ -247,6 +267,27 @@ int md_pair_stats(md_ctx* c, int64_t* listed, int64_t* within_rc) {
     return MD_ERR_ARG;
   }
   return c->eng.pair_stats(0, listed, within_rc, c->stream);
+}
+
+int md_set_tuning(md_ctx* c, int key, int value) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.set_tuning(key, value);
+}
+
+int md_get_tuning(md_ctx* c, int key, int* value) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!value) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  *value = c->eng.get_tuning(key);
+  if (*value < 0) {
+    set_error("unknown tuning key");
+    return MD_ERR_ARG;
+  }
+  return MD_OK;
 }
 
 void md_destroy(md_ctx* c) {
@@ -519,12 +560,61 @@ int md_batch_observables(md_batch* b, double* out) {
   return MD_OK;
 }
 
+int md_batch_kinetic_energy(md_batch* b, double* ke) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!ke) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  const int ns = b->eng.nsys();
+  std::vector<double> o3((size_t)(3 * ns));
+  if ((r = b->eng.observables(o3.data(), b->stream, false))) return r;
+  for (int k = 0; k < ns; ++k) {
+    const ljmd::SysHost& h = b->eng.sys(k);
+    ke[k] = (h.used && h.active) ? o3[3 * k + 2] : 0.0;
+  }
+  return MD_OK;
+}
+
+int md_batch_scale_velocities(md_batch* b, const double* factor) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!factor) {
+    set_error("null factor array");
+    return MD_ERR_ARG;
+  }
+  std::vector<double> f(factor, factor + b->eng.nsys());
+  return b->eng.scale_velocities(f, b->stream);
+}
+
 int md_batch_stats(md_batch* b, int id, int64_t* rebuilds, int64_t* steps) {
   int r = check_batch(b);
   if (r) return r;
   if ((r = check_id(b, id))) return r;
   if (rebuilds) *rebuilds = b->eng.sys(id).rebuilds;
   if (steps) *steps = b->eng.sys(id).steps;
+  return MD_OK;
+}
+
+int md_batch_set_tuning(md_batch* b, int key, int value) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_tuning(key, value);
+}
+
+int md_batch_get_tuning(md_batch* b, int key, int* value) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!value) {
+    set_error("null output");
+    return MD_ERR_ARG;
+  }
+  *value = b->eng.get_tuning(key);
+  if (*value < 0) {
+    set_error("unknown tuning key");
+    return MD_ERR_ARG;
+  }
   return MD_OK;
 }
 

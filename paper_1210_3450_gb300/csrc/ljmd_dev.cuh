@@ -95,8 +95,17 @@ struct DevArrays {
   SysStatus* status;
   unsigned long long* disp2;  // per system: max squared displacement (double bits)
   const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
+  const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
   const int32_t* tile_sys;  // system of each global tile
   int32_t ntiles;
+};
+
+// Launch shapes of the hot kernels (threads per block; partner groups of four
+// per FP32 iteration), chosen by the autotuner.
+struct Tuning {
+  int step_block = 128;
+  int step_groups = 2;
+  int list_block = 128;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -104,17 +113,18 @@ struct DevArrays {
 // systems (or of systems not rebuilding, for the rebuild kernels) return early.
 
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
-void launch_cell_scan(const DevArrays& a, int nsys, cudaStream_t s);
+void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
 void launch_scatter(const DevArrays& a, cudaStream_t s);
-void launch_cell_sort(const DevArrays& a, int nsys, int64_t max_cells, cudaStream_t s);
+void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, cudaStream_t s);
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
-void launch_build_list(const DevArrays& a, int cur, cudaStream_t s);
-void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags,
+void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
+void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s);
-void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags,
+void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s);
-void launch_pe_virial(const DevArrays& a, int cur, cudaStream_t s);
+void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, cudaStream_t s);
+void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s);
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s);
 void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, cudaStream_t s);
 void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n,

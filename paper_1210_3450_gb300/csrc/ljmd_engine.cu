@@ -92,6 +92,31 @@ Engine::~Engine() {
   for (TimedPair& p : ev_pending_) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
 }
 
+int Engine::set_tuning(int key, int value) {
+  switch (key) {
+    case 0:
+      if (value != 64 && value != 128 && value != 256) break;
+      tuning_.step_block = value;
+      return kOK;
+    case 1:
+      if (value != 1 && value != 2) break;
+      tuning_.step_groups = value;
+      return kOK;
+    case 2:
+      if (value != 64 && value != 128 && value != 256) break;
+      tuning_.list_block = value;
+      return kOK;
+    default:
+      break;
+  }
+  set_error("unknown tuning key or value");
+  return kErrArg;
+}
+
+int Engine::get_tuning(int key) const {
+  return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block : -1;
+}
+
 int Engine::set_timing(bool on) {
   timing_ = on;
   for (int k = 0; k < 3; ++k) { t_ms_[k] = 0.0; t_count_[k] = 0; }
@@ -323,7 +348,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_params_, ns));
   CKR(dmalloc(&d_status_, ns));
   CKR(dmalloc(&d_disp2_, ns));
-  CKR(dmalloc(&d_rebuild_, ns));
+  CKR(dmalloc(&d_rebuild_, 2 * ns));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
   CKR(dmalloc(&d_pairs_, 2 * ns));
@@ -333,7 +358,7 @@ int Engine::alloc_arrays() {
   CK(cudaMemset(d_tile_sys_, 0xff, sizeof(int32_t) * T));
   CK(cudaMallocHost((void**)&h_status_, sizeof(SysStatus) * ns));
   CK(cudaMallocHost((void**)&h_disp2_, sizeof(unsigned long long) * ns));
-  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * ns));
+  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * 2 * ns));
   CK(cudaMallocHost((void**)&h_obs_, sizeof(double) * 3 * ns));
   return upload_params();
 }
@@ -487,6 +512,7 @@ DevArrays Engine::arrays() const {
   a.status = d_status_;
   a.disp2 = d_disp2_;
   a.rebuild = d_rebuild_;
+  a.rebuild_ids = d_rebuild_ + nsys();
   a.tile_sys = d_tile_sys_;
   a.ntiles = ntiles_;
   return a;
@@ -545,20 +571,26 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
   if (which.empty()) return kOK;
   for (int attempt = 0; attempt < 4; ++attempt) {
     for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = 0;
-    for (int k : which) h_rebuild_[k] = 1;
-    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * nsys(), cudaMemcpyHostToDevice, s));
+    int64_t reb_cells = 1;
+    for (size_t q = 0; q < which.size(); ++q) {
+      h_rebuild_[which[q]] = 1;
+      h_rebuild_[nsys() + q] = which[q];
+      reb_cells = std::max(reb_cells, sys_[which[q]].ncell);
+    }
+    const int nreb = (int)which.size();
+    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (nsys() + nreb), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(d_status_, 0, sizeof(SysStatus) * nsys(), s));
     const DevArrays a = arrays();
     tmark_begin(kTBin, s);
     launch_cell_count(a, cur_, s);
-    launch_cell_scan(a, nsys(), s);
+    launch_cell_scan(a, nreb, s);
     launch_scatter(a, s);
-    launch_cell_sort(a, nsys(), max_cells_, s);
+    launch_cell_sort(a, cur_, nreb, reb_cells, s);
     launch_gather(a, cur_, s);
     launch_copyback(a, cur_, s);
     tmark_end(s);
     tmark_begin(kTList, s);
-    launch_build_list(a, cur_, s);
+    launch_build_list(a, cur_, tuning_, s);
     tmark_end(s);
     CKL();
     n_launch_ += 7;
@@ -626,8 +658,8 @@ int Engine::ensure_lists(cudaStream_t s) {
 int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
   const DevArrays a = arrays();
   tmark_begin(kTStep, s);
-  if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, s);
-  else launch_step_fp64(a, cur_, ka, kb, flags, s);
+  if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
+  else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, s);
   tmark_end(s);
   CKL();
   n_launch_ += 1;
@@ -727,15 +759,26 @@ int Engine::forces_dev(int k, double* f, cudaStream_t s) {
   return kOK;
 }
 
-int Engine::observables(double* out3, cudaStream_t s) {
-  CKR(ensure_lists(s));
+int Engine::observables(double* out3, cudaStream_t s, bool with_pairs) {
+  if (with_pairs) CKR(ensure_lists(s));
   const DevArrays a = arrays();
-  launch_pe_virial(a, cur_, s);
+  launch_pe_virial(a, cur_, with_pairs ? 1 : 0, s);
   launch_reduce_obs(a, cur_, nsys(), d_obs_, s);
   CKL();
   CK(cudaMemcpyAsync(h_obs_, d_obs_, sizeof(double) * 3 * nsys(), cudaMemcpyDeviceToHost, s));
   CKR(sync_check(s));
   std::memcpy(out3, h_obs_, sizeof(double) * 3 * nsys());
+  return kOK;
+}
+
+int Engine::scale_velocities(const std::vector<double>& factor, cudaStream_t s) {
+  if ((int)factor.size() != nsys()) { set_error("one factor per system required"); return kErrArg; }
+  for (double f : factor)
+    if (!std::isfinite(f)) { set_error("scale factor must be finite"); return kErrArg; }
+  CK(cudaMemcpyAsync(d_obs_, factor.data(), sizeof(double) * nsys(), cudaMemcpyHostToDevice, s));
+  launch_scale_v(arrays(), d_obs_, s);
+  CKL();
+  CKR(sync_check(s));
   return kOK;
 }
 

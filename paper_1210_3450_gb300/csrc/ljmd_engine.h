@@ -109,7 +109,9 @@ class Engine {
   // entries of inactive ids are ignored).
   int step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s);
   // Observables (pe, virial, ke) of every active system into host out3[3 * nsys].
-  int observables(double* out3, cudaStream_t s);
+  int observables(double* out3, cudaStream_t s, bool with_pairs = true);
+  // v *= factor[id] for every active system (factor: nsys doubles).
+  int scale_velocities(const std::vector<double>& factor, cudaStream_t s);
   // Rebuild the lists of all active systems now.
   int build_lists(cudaStream_t s);
   // Inspection (host arrays, caller order).
@@ -118,6 +120,10 @@ class Engine {
   int get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s);
 
   int set_active(int k, bool on);
+  // Launch shapes: key 0 = step-kernel threads per block (64/128/256), 1 = FP32
+  // partner groups per iteration (1/2), 2 = list-build threads per block.
+  int set_tuning(int key, int value);
+  int get_tuning(int key) const;
   // Per-kernel-class device times (CUDA events on the launching stream).
   int set_timing(bool on);
   void get_timing(double* out8) const;
@@ -144,6 +150,7 @@ class Engine {
   void tmark_end(cudaStream_t s);
   void collect_timing();
   struct TimedPair { cudaEvent_t a, b; int kind; };
+  Tuning tuning_{};
   bool timing_ = false;
   std::vector<cudaEvent_t> ev_free_;
   std::vector<TimedPair> ev_pending_;
@@ -167,7 +174,7 @@ class Engine {
   SysParams* d_params_ = nullptr;
   SysStatus* d_status_ = nullptr;
   unsigned long long* d_disp2_ = nullptr;
-  int32_t* d_rebuild_ = nullptr;
+  int32_t* d_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;
   unsigned long long* d_pairs_ = nullptr;
@@ -176,7 +183,7 @@ class Engine {
   // pinned host mirrors
   SysStatus* h_status_ = nullptr;
   unsigned long long* h_disp2_ = nullptr;
-  int32_t* h_rebuild_ = nullptr;
+  int32_t* h_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
   double* h_obs_ = nullptr;
 };
 

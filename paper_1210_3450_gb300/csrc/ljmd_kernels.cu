@@ -119,9 +119,9 @@ __global__ void k_cell_count(DevArrays a, int cur) {
 
 // Exclusive scan of the cell counts of one system per block; the counts are
 // then reset to serve as fill counters of the scatter.
-__global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nsys) {
-  const int sys = blockIdx.x;
-  if (sys >= nsys) return;
+__global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
+  if ((int)blockIdx.x >= nreb) return;
+  const int sys = a.rebuild_ids[blockIdx.x];
   const SysParams P = a.params[sys];
   if (!P.active || !a.rebuild[sys]) return;
   __shared__ int wsum[32];
@@ -175,10 +175,12 @@ __global__ void k_scatter(DevArrays a) {
   a.perm[P.p_off + pos] = t.local;
 }
 
-// Order the particles of each cell by caller index (makes the scatter stable
-// and the whole build deterministic). Insertion sort: cells hold tens of particles.
-__global__ void k_cell_sort(DevArrays a) {
-  const int sys = blockIdx.y;
+// Order the particles of each cell by x, ties by caller index (deterministic).
+// A row of neighbouring cells along x is then sorted by x as a whole, which lets
+// the list build restrict each row to the window |x_j - x_i| < rl.
+// Insertion sort: cells hold tens of particles.
+__global__ void k_cell_sort(DevArrays a, int cur) {
+  const int sys = a.rebuild_ids[blockIdx.y];
   const SysParams P = a.params[sys];
   if (!P.active || !a.rebuild[sys] || P.nc == 1) return;
   const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
@@ -188,12 +190,17 @@ __global__ void k_cell_sort(DevArrays a) {
   a.ccount[P.c_off + c] = 0;  // ready for the next binning
   int32_t* pm = a.perm + P.p_off;
   const int32_t* id = a.id + P.p_off;
+  const double4_32a* xs = a.x[cur] + P.p_off;
   for (int k = lo + 1; k < hi; ++k) {
     const int32_t pk = pm[k];
-    const int32_t key = id[pk];
+    const double kx = xs[pk].x;
+    const int32_t kid = id[pk];
     int m = k - 1;
-    while (m >= lo && id[pm[m]] > key) {
-      pm[m + 1] = pm[m];
+    while (m >= lo) {
+      const int32_t pmm = pm[m];
+      const double mx = xs[pmm].x;
+      if (mx < kx || (mx == kx && id[pmm] < kid)) break;
+      pm[m + 1] = pmm;
       --m;
     }
     pm[m + 1] = pk;
@@ -218,9 +225,10 @@ __global__ void k_copyback(DevArrays a, int cur) {
   const double4_32a x = a.xtmp[t.s];
   a.x[cur][t.s] = x;
   a.xref[t.s] = x;
-  const int4 q = fixed4(x, P.qscale);
-  a.xq[cur][t.s] = q;
+  int4 q = fixed4(x, P.qscale);
   a.xqref[t.s] = q;
+  q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
+  a.xq[cur][t.s] = q;
   a.v[t.s] = a.vtmp[t.s];
   a.id[t.s] = a.idtmp[t.s];
   a.cell[t.s] = a.celltmp[t.s];
@@ -265,13 +273,26 @@ struct ListOut {
 
 // Test the candidates of slot range [lo, hi) (all with image `code`, or 0xff for
 // the per-pair minimum image) against particle li and append the partners.
+// With `sorted`, the range is ordered by x (key: float x in q.w) and only the
+// window xlo <= x_j < xhi can hold partners (|dx| < rl, bounds widened by a
+// margin); the first candidate is found by bisection and the sweep stops at xhi.
 __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const double4_32a* __restrict__ xs,
                                             int lo, int hi, unsigned code, int li, const int4& qi,
-                                            const double4_32a& xi, const LBParams& P, ListOut& o) {
+                                            const double4_32a& xi, const LBParams& P, ListOut& o,
+                                            bool sorted, float xlo, float xhi) {
+  if (sorted) {
+    int b = hi;
+    while (lo < b) {
+      const int m = (lo + b) >> 1;
+      if (__int_as_float(qs[m].w) < xlo) lo = m + 1;
+      else b = m;
+    }
+  }
   int4 qn = lo < hi ? qs[lo] : qi;
   for (int j = lo; j < hi; ++j) {
     const int4 qj = qn;
     if (j + 1 < hi) qn = qs[j + 1];  // issue the next load before this test
+    if (sorted && !(__int_as_float(qj.w) < xhi)) break;
     const float ax = (float)wrapped_diff(qj.x, qi.x);
     const float ay = (float)wrapped_diff(qj.y, qi.y);
     const float az = (float)wrapped_diff(qj.z, qi.z);
@@ -307,7 +328,8 @@ __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const d
 // the pair is certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only
 // the thin shell between needs the FP64 test. The result is identical to always
 // taking it.
-__global__ void __launch_bounds__(kBlock, 8) k_build_list(DevArrays a, int cur) {
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a, int cur) {
   const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= a.ntiles) return;
@@ -324,6 +346,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_build_list(DevArrays a, int cur) 
   const double4_32a xi = xs[li];
   const int4 qi = qs[li];
   LBParams P{Pp->L, Pp->rl2, Pp->rl2q_lo, Pp->rl2q_hi, Pp->n};
+  // half-width of the x window: rl plus a margin far above the float rounding
+  // of the keys (about 1e-7 L)
+  const float wpad = (float)(sqrt(Pp->rl2) + 1e-5 * Pp->L + 1e-6);
   ListOut o{a.nbr + list_word(Pp->l_off, tl, Pp->kmax, lane, 0), 0, Pp->kmax};
   const int nc = Pp->nc;
   const int32_t* cst = a.cstart + Pp->c_off;
@@ -361,7 +386,10 @@ __global__ void __launch_bounds__(kBlock, 8) k_build_list(DevArrays a, int cur) 
     } else {
       lo = 0; hi = P.n; code = 0xffu;
     }
-    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o);
+    // x window of the candidates in this range's own coordinates
+    const float sx = (code & 3u) == 2u ? (float)Pp->L : ((code & 3u) == 1u ? -(float)Pp->L : 0.0f);
+    const float xw = (float)xi.x + sx;
+    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o, nc > 1, xw - wpad, xw + wpad);
   }
   a.ncnt[p_off + li] = o.count < o.kmax ? o.count : o.kmax;
   if (o.count > o.kmax) atomicMax(&a.status[sys].overflow, o.count);
@@ -449,10 +477,13 @@ __device__ __forceinline__ void pair_fp32(const int4& qi, const int4& qj, bool v
 }  // namespace
 
 // FP32-force form: pair arithmetic in FP32 from fixed-point separations (the
-// wrapped integer difference is already the minimum image), four partners per
-// 16-byte list load, the next group's load issued before the current group's
-// gathers are used (software pipelining, the role of Algorithm 1's unrolling).
-__global__ void __launch_bounds__(kBlock) k_step_fp32(DevArrays a, int cur, double ka, double kb, int flags) {
+// wrapped integer difference is already the minimum image). Each iteration
+// takes GROUPS x 4 partners (GROUPS 16-byte list loads, then 4 GROUPS gathers in
+// flight at once) and the next iteration's list loads are issued before this
+// iteration's gathers are used (software pipelining, the role of Algorithm 1's
+// unrolling). BLOCK and GROUPS are chosen by the autotuner.
+template <int BLOCK, int GROUPS>
+__global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, double ka, double kb, int flags) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
@@ -472,22 +503,35 @@ __global__ void __launch_bounds__(kBlock) k_step_fp32(DevArrays a, int cur, doub
     const int4 qi = a.xq[cur][t.s];
     const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
     const uint32_t self = (uint32_t)t.local;
+    const uint4 none = make_uint4(self, self, self, self);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     const int ng = (cnt + 3) >> 2;
-    uint4 e = ng > 0 ? __ldg(lp4) : make_uint4(self, self, self, self);
-    for (int g = 0; g < ng; ++g) {
-      const uint4 en = (g + 1 < ng) ? __ldg(lp4 + (int64_t)(g + 1) * kTile) : e;
-      const int rem = cnt - 4 * g;
-      const uint32_t j0 = e.x & kIdxMask;
-      const uint32_t j1 = rem > 1 ? (e.y & kIdxMask) : self;
-      const uint32_t j2 = rem > 2 ? (e.z & kIdxMask) : self;
-      const uint32_t j3 = rem > 3 ? (e.w & kIdxMask) : self;
-      const int4 q0 = qs[j0], q1 = qs[j1], q2 = qs[j2], q3 = qs[j3];
-      pair_fp32(qi, q0, true, qu, rc2, c2x8, fx, fy, fz);
-      pair_fp32(qi, q1, rem > 1, qu, rc2, c2x8, fx, fy, fz);
-      pair_fp32(qi, q2, rem > 2, qu, rc2, c2x8, fx, fy, fz);
-      pair_fp32(qi, q3, rem > 3, qu, rc2, c2x8, fx, fy, fz);
-      e = en;
+    uint4 e[GROUPS];
+#pragma unroll
+    for (int u = 0; u < GROUPS; ++u) e[u] = u < ng ? __ldg(lp4 + (int64_t)u * kTile) : none;
+    for (int g = 0; g < ng; g += GROUPS) {
+      uint4 en[GROUPS];
+#pragma unroll
+      for (int u = 0; u < GROUPS; ++u)
+        en[u] = (g + GROUPS + u < ng) ? __ldg(lp4 + (int64_t)(g + GROUPS + u) * kTile) : none;
+      int4 q[4 * GROUPS];
+      bool ok[4 * GROUPS];
+#pragma unroll
+      for (int u = 0; u < GROUPS; ++u) {
+        const int rem = cnt - 4 * (g + u);
+        ok[4 * u + 0] = rem > 0;
+        ok[4 * u + 1] = rem > 1;
+        ok[4 * u + 2] = rem > 2;
+        ok[4 * u + 3] = rem > 3;
+        q[4 * u + 0] = qs[ok[4 * u + 0] ? (e[u].x & kIdxMask) : self];
+        q[4 * u + 1] = qs[ok[4 * u + 1] ? (e[u].y & kIdxMask) : self];
+        q[4 * u + 2] = qs[ok[4 * u + 2] ? (e[u].z & kIdxMask) : self];
+        q[4 * u + 3] = qs[ok[4 * u + 3] ? (e[u].w & kIdxMask) : self];
+      }
+#pragma unroll
+      for (int m = 0; m < 4 * GROUPS; ++m) pair_fp32(qi, q[m], ok[m], qu, rc2, c2x8, fx, fy, fz);
+#pragma unroll
+      for (int u = 0; u < GROUPS; ++u) e[u] = en[u];
     }
     Fx = fx; Fy = fy; Fz = fz;
   }
@@ -500,7 +544,8 @@ __global__ void __launch_bounds__(kBlock) k_step_fp32(DevArrays a, int cur, doub
 // pair inside rc the reciprocal (3 DFMA after an integer-built FP32 seed),
 // powers (3), factor (2) and accumulation (3). The cutoff test compares bit
 // patterns (r^2 >= 0), so it costs no FP64 instruction.
-__global__ void __launch_bounds__(kBlock) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
@@ -552,13 +597,13 @@ __global__ void __launch_bounds__(kBlock) k_step_fp64(DevArrays a, int cur, doub
 // Per particle: 1/2 sum_j V(r) and 1/2 sum_j -r V'(r) over listed partners with
 // r < rc (the full list counts each pair twice), and 1/2 |v|^2; each tile sums
 // its 32 values in a fixed shuffle order into tile_obs[3 t ...].
-__global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur) {
+__global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
   const int lane = threadIdx.x & 31;
   double pe = 0.0, w = 0.0, ke = 0.0;
-  if (t.act) {
+  if (t.act && with_pairs) {
     const double4_32a xi = a.x[cur][t.s];
     const double4_32a* xs = a.x[cur] + P.p_off;
     const int cnt = a.ncnt[t.s];
@@ -580,6 +625,8 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur) {
     }
     pe *= 0.5;
     w *= 0.5;
+  }
+  if (t.act) {
     const double4_32a v = a.v[t.s];
     ke = 0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
   }
@@ -684,29 +731,74 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
   k_cell_count<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
 }
-void launch_cell_scan(const DevArrays& a, int nsys, cudaStream_t s) {
-  k_cell_scan<<<nsys, 1024, 0, s>>>(a, nsys);
+void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
+  k_cell_scan<<<nreb, 1024, 0, s>>>(a, nreb);
 }
 void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<tile_blocks(a), kBlock, 0, s>>>(a); }
-void launch_cell_sort(const DevArrays& a, int nsys, int64_t max_cells, cudaStream_t s) {
-  dim3 g((unsigned)((max_cells + 127) / 128), (unsigned)nsys);
-  k_cell_sort<<<g, 128, 0, s>>>(a);
+void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, cudaStream_t s) {
+  dim3 g((unsigned)((max_cells + 127) / 128), (unsigned)nreb);
+  k_cell_sort<<<g, 128, 0, s>>>(a, cur);
 }
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<tile_blocks(a), kBlock, 0, s>>>(a, cur); }
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
   k_copyback<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
 }
-void launch_build_list(const DevArrays& a, int cur, cudaStream_t s) {
-  k_build_list<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+namespace {
+inline unsigned blocks_of(const DevArrays& a, int block) {
+  return (unsigned)(((int64_t)a.ntiles * kTile + block - 1) / block);
 }
-void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
-  k_step_fp64<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+}  // namespace
+
+void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s) {
+  switch (tu.list_block) {
+    case 64: k_build_list<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
+    case 256: k_build_list<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
+    default: k_build_list<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+  }
 }
-void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, cudaStream_t s) {
-  k_step_fp32<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, ka, kb, flags);
+void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
+                      cudaStream_t s) {
+  switch (tu.step_block) {
+    case 64: k_step_fp64<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, ka, kb, flags); break;
+    case 256: k_step_fp64<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, ka, kb, flags); break;
+    default: k_step_fp64<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, ka, kb, flags); break;
+  }
 }
-void launch_pe_virial(const DevArrays& a, int cur, cudaStream_t s) {
-  k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
+                      cudaStream_t s) {
+  const int b = tu.step_block, g = tu.step_groups;
+#define LJMD_STEP32(B, G) k_step_fp32<B, G><<<blocks_of(a, B), B, 0, s>>>(a, cur, ka, kb, flags)
+  if (g == 2) {
+    if (b == 64) LJMD_STEP32(64, 2);
+    else if (b == 256) LJMD_STEP32(256, 2);
+    else LJMD_STEP32(128, 2);
+  } else {
+    if (b == 64) LJMD_STEP32(64, 1);
+    else if (b == 256) LJMD_STEP32(256, 1);
+    else LJMD_STEP32(128, 1);
+  }
+#undef LJMD_STEP32
+}
+void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, cudaStream_t s) {
+  k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, with_pairs);
+}
+
+// v *= factor for every particle of the systems with scale[sys] != 1.
+__global__ void k_scale_v(DevArrays a, const double* __restrict__ scale) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !t.act) return;
+  const double f = scale[t.sys];
+  if (f == 1.0) return;
+  double4_32a v = a.v[t.s];
+  v.x *= f;
+  v.y *= f;
+  v.z *= f;
+  a.v[t.s] = v;
+}
+
+void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s) {
+  k_scale_v<<<tile_blocks(a), kBlock, 0, s>>>(a, scale);
 }
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s) {
   k_pair_stats<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, out2);

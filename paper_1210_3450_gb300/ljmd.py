@@ -25,6 +25,11 @@ MD_ERR_STATE = -7
 MD_FP64 = 0
 MD_FP32_FORCE = 1
 MD_MAX_N = (1 << 26) - 1
+MD_TUNE_STEP_BLOCK = 0
+MD_TUNE_STEP_GROUPS = 1
+MD_TUNE_LIST_BLOCK = 2
+TUNING_KEYS = {"step_block": MD_TUNE_STEP_BLOCK, "step_groups": MD_TUNE_STEP_GROUPS,
+               "list_block": MD_TUNE_LIST_BLOCK}
 
 _ERRNAMES = {v: k for k, v in dict(MD_ERR_ARG=-1, MD_ERR_OOM=-2, MD_ERR_LIST_OVERFLOW=-3,
                                    MD_ERR_NONFINITE=-4, MD_ERR_TIMEOUT=-5, MD_ERR_CUDA=-6,
@@ -53,6 +58,10 @@ SIGNATURES = {
     "md_forces_dev": (C.c_int, [_P, _P, _P]),
     "md_observables": (C.c_int, [_P, _PD, _PD, _PD, _PD, _PD]),
     "md_stats": (C.c_int, [_P, _PI64, _PI64]),
+    "md_kinetic_energy": (C.c_int, [_P, _PD]),
+    "md_scale_velocities": (C.c_int, [_P, C.c_double]),
+    "md_batch_kinetic_energy": (C.c_int, [_P, _PD]),
+    "md_batch_scale_velocities": (C.c_int, [_P, _PD]),
     "md_build_list": (C.c_int, [_P]),
     "md_get_cells": (C.c_int, [_P, _PI32, _PI32]),
     "md_list_size": (C.c_int, [_P, _PI64]),
@@ -61,6 +70,10 @@ SIGNATURES = {
     "md_set_timing": (C.c_int, [_P, C.c_int]),
     "md_get_timing": (C.c_int, [_P, _PD]),
     "md_forces_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, _P, _P]),
+    "md_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "md_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "md_batch_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "md_batch_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "md_destroy": (None, [_P]),
     "md_batch_create": (C.c_int, [C.c_int, _P, C.c_int, C.POINTER(_P)]),
     "md_batch_create_arena": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int, C.POINTER(_P)]),
@@ -218,6 +231,14 @@ class LJSystem:
         _check(_lib.md_stats(self._h, C.byref(r), C.byref(s)))
         return dict(rebuilds=r.value, steps=s.value)
 
+    def kinetic_energy(self) -> float:
+        ke = C.c_double()
+        _check(_lib.md_kinetic_energy(self._h, C.byref(ke)))
+        return ke.value
+
+    def scale_velocities(self, factor: float):
+        _check(_lib.md_scale_velocities(self._h, float(factor)))
+
     def build_list(self):
         _check(_lib.md_build_list(self._h))
 
@@ -240,6 +261,18 @@ class LJSystem:
 
     def set_timing(self, on: bool = True):
         _check(_lib.md_set_timing(self._h, 1 if on else 0))
+
+    def set_tuning(self, **kw):
+        for k, v in kw.items():
+            _check(_lib.md_set_tuning(self._h, TUNING_KEYS[k], int(v)))
+
+    def get_tuning(self) -> dict:
+        out = {}
+        for k, key in TUNING_KEYS.items():
+            v = C.c_int()
+            _check(_lib.md_get_tuning(self._h, key, C.byref(v)))
+            out[k] = v.value
+        return out
 
     def get_timing(self) -> dict:
         out = np.zeros(8)
@@ -395,8 +428,36 @@ class LJBatch:
         _check(_lib.md_batch_stats(self._h, int(sid), C.byref(r), C.byref(s)))
         return dict(rebuilds=r.value, steps=s.value)
 
+    def kinetic_energy(self) -> np.ndarray:
+        ke = np.zeros(self.max_systems)
+        _check(_lib.md_batch_kinetic_energy(self._h, _pd(ke)))
+        return ke
+
+    def scale_velocities(self, factor):
+        f = np.ones(self.max_systems)
+        if np.isscalar(factor):
+            f[:] = float(factor)
+        elif isinstance(factor, dict):
+            for k, val in factor.items():
+                f[k] = val
+        else:
+            f[:len(factor)] = factor
+        _check(_lib.md_batch_scale_velocities(self._h, _pd(f)))
+
     def set_timing(self, on: bool = True):
         _check(_lib.md_batch_set_timing(self._h, 1 if on else 0))
+
+    def set_tuning(self, **kw):
+        for k, v in kw.items():
+            _check(_lib.md_batch_set_tuning(self._h, TUNING_KEYS[k], int(v)))
+
+    def get_tuning(self) -> dict:
+        out = {}
+        for k, key in TUNING_KEYS.items():
+            v = C.c_int()
+            _check(_lib.md_batch_get_tuning(self._h, key, C.byref(v)))
+            out[k] = v.value
+        return out
 
     def get_timing(self) -> dict:
         out = np.zeros(8)

@@ -29,6 +29,10 @@ def main(argv=None):
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--step-block", type=int, default=None)
+    p.add_argument("--step-groups", type=int, default=None)
+    p.add_argument("--list-block", type=int, default=None)
+    p.add_argument("--autotune", action="store_true")
     a = p.parse_args(argv)
     import lj_inputs as li
     from paper_1210_3450_gb300 import build
@@ -40,13 +44,23 @@ def main(argv=None):
     v = li.maxwell_boltzmann(n, a.temperature, 1000 + a.cells)
     mode = MD_FP32_FORCE if a.precision == "fp32" else MD_FP64
     with LJSystem(box, n, a.rc, a.skin, mode) as s:
+        tun = {k: val for k, val in dict(step_block=a.step_block, step_groups=a.step_groups,
+                                         list_block=a.list_block).items() if val is not None}
+        if tun:
+            s.set_tuning(**tun)
         s.set_state(x, v)
+        tuned = None
+        if a.autotune:
+            from paper_1210_3450_gb300 import autotune
+            tuned = autotune.tune(s, a.dt, cache=None, fp32=(mode == MD_FP32_FORCE))
         s.step(a.warmup, a.dt)
         s.set_timing(True)
         s.step(a.steps, a.dt)
         t = s.get_timing()
         listed, inside = s.pair_stats()
     t.update(n=n, listed_per_particle=listed / n, within_rc_per_particle=inside / n)
+    if tuned:
+        t["autotune"] = tuned
     print(json.dumps(t))
 
 

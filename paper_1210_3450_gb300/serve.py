@@ -48,7 +48,7 @@ def arena_for_budget(budget_bytes: int, max_systems: int = 4096, list_share: flo
     return dict(slots=slots, cells=cells, list_words=list_words, max_systems=max_systems)
 
 
-@dataclass
+@dataclass(eq=False)
 class Request:
     id: int
     arrival: float
@@ -94,6 +94,7 @@ class MDServer:
         self.done: list[Request] = []
         self.particle_steps = 0
         self.gpu_busy = 0.0
+        self.t0 = self.clock()  # times of requests are seconds since t0
 
     def close(self):
         self.batch.close()
@@ -141,7 +142,7 @@ class MDServer:
                 finished.append(sid)
         if finished:
             obs = self.batch.observables()
-            now = self.clock()
+            now = self.clock() - self.t0
             for sid in finished:
                 r = self.running.pop(sid)
                 o = obs[sid]
@@ -158,7 +159,7 @@ class MDServer:
         """Replay requests at their arrival times (seconds from the start) in real
         time; stop when all are done or drain_limit seconds after the last arrival."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        t0 = self.clock()
+        self.t0 = t0 = self.clock()
         i = 0
         last_arrival = reqs[-1].arrival if reqs else 0.0
         while i < len(reqs) or self.pending or self.running:
@@ -187,7 +188,8 @@ class MDServer:
         done = [r for r in self.done if "rejected" not in r.result]
         lat = np.array([r.finished - r.arrival for r in done]) if done else np.array([math.nan])
         wait = np.array([r.admitted - r.arrival for r in done]) if done else np.array([math.nan])
-        left = [r for r in reqs if r not in self.done]
+        done_ids = {id(r) for r in self.done}
+        left = [r for r in reqs if id(r) not in done_ids]
         left_work = sum(r.n * (r.remaining if r.sid >= 0 and not math.isnan(r.admitted) else r.steps)
                         for r in left)
         rate = self.particle_steps / wall if wall > 0 else math.nan

@@ -1,0 +1,52 @@
+"""Serving: runs that arrive while others are on the GPU are admitted as arena
+space frees up, advance together, and each result is bit-for-bit the result of
+the same run alone (FP32-force mode, the serving default)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_served_results_equal_alone(ljmd):
+    from paper_1210_3450_gb300 import serve
+    reqs = []
+    rng = np.random.default_rng(5)
+    for k in range(10):
+        n = int(rng.integers(300, 5000))
+        reqs.append(serve.Request(id=k, arrival=0.002 * k, n=n, rho=float(rng.uniform(0.6, 0.85)),
+                                  temperature=float(rng.uniform(0.72, 1.2)),
+                                  steps=int(rng.integers(30, 150)), seed=1000 + k))
+    # budget for roughly three of these runs at a time: later ones must wait
+    budget = 3 * 5000 * 900
+    srv = serve.MDServer(budget, precision=ljmd.MD_FP32_FORCE, chunk=40, keep_state=True)
+    try:
+        summary = srv.run(reqs)
+    finally:
+        srv.close()
+    assert summary["completed"] == len(reqs)
+    waited = [r for r in srv.done if r.admitted > min(q.finished for q in srv.done)]
+    assert waited, "the budget should have made some requests wait for space"
+    assert all(r.finished >= r.admitted >= r.arrival for r in srv.done)
+    for r in srv.done:
+        x0, v0 = serve.initial_state(r)
+        with ljmd.LJSystem(r.box, r.n, r.rc, r.skin, ljmd.MD_FP32_FORCE) as s:
+            s.set_state(x0, v0)
+            s.step(r.steps, r.dt)
+            x, v = s.get_state()
+            o = s.observables()
+            st = s.stats()
+        np.testing.assert_array_equal(r.result["x"], x)
+        np.testing.assert_array_equal(r.result["v"], v)
+        assert r.result["pe"] == o["pe"] and r.result["ke"] == o["ke"]
+        assert r.result["rebuilds"] == st["rebuilds"]
+
+
+def test_request_larger_than_arena_is_rejected(ljmd):
+    from paper_1210_3450_gb300 import serve
+    r = serve.Request(id=0, arrival=0.0, n=200000, rho=0.8, temperature=1.0, steps=10, seed=1)
+    srv = serve.MDServer(10_000_000, precision=ljmd.MD_FP32_FORCE)
+    try:
+        s = srv.run([r])
+    finally:
+        srv.close()
+    assert s["rejected"] == 1 and s["completed"] == 0
