@@ -177,11 +177,15 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
  *   MD_TUNE_STEP_BLOCK   threads per block of the force + integration kernel: 64, 128, 256
  *   MD_TUNE_STEP_GROUPS  FP32-force partners loaded per iteration, in groups of 4: 1, 2
  *   MD_TUNE_LIST_BLOCK   threads per block of the pair-list build: 64, 128, 256
- * Defaults 128 / 2 / 128. The autotuner (paper_1210_3450_gb300.autotune) times the
+ *   MD_TUNE_LIST_VARIANT pair-list build variant: bit 0 prunes neighbour rows and
+ *                        narrows their x windows by the y / z distance to the row,
+ *                        bit 1 writes list entries four at a time (0..3)
+ * Defaults 128 / 2 / 128 / 0. The autotuner (paper_1210_3450_gb300.autotune) times the
  * choices on the caller's own systems and sets the fastest. */
 #define MD_TUNE_STEP_BLOCK 0
 #define MD_TUNE_STEP_GROUPS 1
 #define MD_TUNE_LIST_BLOCK 2
+#define MD_TUNE_LIST_VARIANT 3
 MD_API int md_set_tuning(md_ctx* ctx, int key, int value);
 MD_API int md_get_tuning(md_ctx* ctx, int key, int* value);
 

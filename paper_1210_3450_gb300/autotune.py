@@ -23,6 +23,7 @@ DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
 STEP_BLOCKS = (64, 128, 256)
 STEP_GROUPS = (1, 2)
 LIST_BLOCKS = (64, 128, 256)
+LIST_VARIANTS = (0, 1, 2, 3)
 
 
 def shape_key(precision: int, particles: int, density: float, systems: int) -> str:
@@ -68,18 +69,18 @@ def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None 
     blk, grp = min(step_choices, key=lambda c: results[f"step{c[0]}x{c[1]}"])
     system.set_tuning(step_block=blk, step_groups=grp)
     list_times = {}
-    for lb in LIST_BLOCKS:
-        system.set_tuning(list_block=lb)
+    for lb, lv in itertools.product(LIST_BLOCKS, LIST_VARIANTS):
+        system.set_tuning(list_block=lb, list_variant=lv)
         system.set_timing(True)
         system.build_list() if hasattr(system, "build_list") else None
         system.step(steps, dt)
         t = system.get_timing()
         if t["list_launches"]:
-            list_times[lb] = t["list_ms"] / t["list_launches"]
-    lbest = min(list_times, key=list_times.get) if list_times else 128
-    system.set_tuning(list_block=lbest)
-    out = dict(tuning=dict(step_block=blk, step_groups=grp, list_block=lbest),
-               step_ms=results, list_ms={str(k): v for k, v in list_times.items()})
+            list_times[(lb, lv)] = t["list_ms"] / t["list_launches"]
+    lbest, lvar = min(list_times, key=list_times.get) if list_times else (128, 0)
+    system.set_tuning(list_block=lbest, list_variant=lvar)
+    out = dict(tuning=dict(step_block=blk, step_groups=grp, list_block=lbest, list_variant=lvar),
+               step_ms=results, list_ms={f"{k[0]}v{k[1]}": v for k, v in list_times.items()})
     if cache and key:
         data = _load(cache)
         data[key] = out

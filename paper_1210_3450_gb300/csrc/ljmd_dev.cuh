@@ -43,6 +43,9 @@ struct SysParams {
   float rl2q_hi;     // rl^2 (1 + 1e-5) in fixed-point units^2: certainly outside above
   float rc2f;        // rc^2 as float (FP32 force cutoff)
   float c2f;         // c2 as float
+  float rlf;         // rc + skin as float
+  float csf;         // cell side L / nc as float
+  float wmargin;     // margin of the list build's geometric windows (1e-5 L + 1e-6)
   int64_t p_off;     // first slot
   int64_t c_off;     // first cell (cell arrays hold ncell + 1 entries per system)
   int64_t l_off;     // first list word
@@ -52,7 +55,6 @@ struct SysParams {
   int32_t t_off;     // first global tile
   int32_t ntiles;    // tiles of this system
   int32_t active;    // 1 if the system takes part in the current launches
-  int32_t pad_;
 };
 
 // Per-system status words written by kernels and read by the host.
@@ -106,6 +108,7 @@ struct Tuning {
   int step_block = 128;
   int step_groups = 2;
   int list_block = 128;
+  int list_variant = 0;  // bit 0: row pruning by y / z distance; bit 1: 16-byte list writes
 };
 
 // ---------------------------------------------------------------- launchers

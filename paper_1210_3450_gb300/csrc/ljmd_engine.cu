@@ -106,6 +106,10 @@ int Engine::set_tuning(int key, int value) {
       if (value != 64 && value != 128 && value != 256) break;
       tuning_.list_block = value;
       return kOK;
+    case 3:
+      if (value < 0 || value > 3) break;
+      tuning_.list_variant = value;
+      return kOK;
     default:
       break;
   }
@@ -114,7 +118,8 @@ int Engine::set_tuning(int key, int value) {
 }
 
 int Engine::get_tuning(int key) const {
-  return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block : -1;
+  return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block
+         : key == 3 ? tuning_.list_variant : -1;
 }
 
 int Engine::set_timing(bool on) {
@@ -492,6 +497,9 @@ int Engine::upload_params(int only) {
     P.rl2q_hi = (float)(P.rl2 * P.qscale * P.qscale * (1.0 + 1e-5));
     P.rc2f = (float)P.rc2;
     P.c2f = (float)h.c2;
+    P.rlf = (float)h.rl;
+    P.csf = (float)(h.spec.L / h.nc);
+    P.wmargin = (float)(1e-5 * h.spec.L + 1e-6);
     P.p_off = h.p_off;
     P.c_off = h.c_off;
     P.l_off = h.l_off;

@@ -191,14 +191,15 @@ __global__ void k_cell_sort(DevArrays a, int cur) {
   int32_t* pm = a.perm + P.p_off;
   const int32_t* id = a.id + P.p_off;
   const double4_32a* xs = a.x[cur] + P.p_off;
+  // keys: x >= 0 (wrapped), so its bit pattern orders like the value
   for (int k = lo + 1; k < hi; ++k) {
     const int32_t pk = pm[k];
-    const double kx = xs[pk].x;
+    const long long kx = __double_as_longlong(xs[pk].x);
     const int32_t kid = id[pk];
     int m = k - 1;
     while (m >= lo) {
       const int32_t pmm = pm[m];
-      const double mx = xs[pmm].x;
+      const long long mx = __double_as_longlong(xs[pmm].x);
       if (mx < kx || (mx == kx && id[pmm] < kid)) break;
       pm[m + 1] = pmm;
       --m;
@@ -265,20 +266,67 @@ struct LBParams {
   int n;
 };
 
+// List writer: entries are collected four at a time and stored as one 16-byte
+// word group (the list layout keeps a particle's entries 4k..4k+3 adjacent).
+template <bool BUF>
 struct ListOut {
   uint32_t* out;
   int count;
   int kmax;
+  uint4 buf;
+  __device__ __forceinline__ void push(uint32_t e) {
+    if (!BUF) {  // one 4-byte store per entry
+      if (count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
+      ++count;
+      return;
+    }
+    const int slot = count & 3;
+    if (slot == 0) buf.x = e;
+    else if (slot == 1) buf.y = e;
+    else if (slot == 2) buf.z = e;
+    else buf.w = e;
+    if (slot == 3 && count < kmax) *(uint4*)(out + (int64_t)(count >> 2) * (4 * kTile)) = buf;
+    ++count;
+  }
+  __device__ __forceinline__ void flush() {
+    if (BUF && (count & 3) != 0 && count < kmax) *(uint4*)(out + (int64_t)(count >> 2) * (4 * kTile)) = buf;
+  }
 };
 
+// Append candidate j to the list if it is inside: below rl2q_lo the FP32 bound
+// decides, in the shell (or for per-pair images) the exact FP64 test decides.
+template <class Out>
+__device__ __forceinline__ void accept(const double4_32a* __restrict__ xs, int j, float r2q, unsigned code,
+                                       const double4_32a& xi, const LBParams& P, Out& o) {
+  unsigned cj = code;
+  bool inside = true;
+  if (!(r2q < P.rl2q_lo) || code == 0xffu) {
+    const double4_32a xj = xs[j];
+    const unsigned r = exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, P.L, P.rl2);
+    cj = r & 0xffu;
+    inside = (r >> 8) & 1u;
+  }
+  if (inside) o.push((uint32_t)j | (cj << kIdxBits));
+}
+
+__device__ __forceinline__ float r2_fixed(const int4& qj, const int4& qi) {
+  const float ax = (float)wrapped_diff(qj.x, qi.x);
+  const float ay = (float)wrapped_diff(qj.y, qi.y);
+  const float az = (float)wrapped_diff(qj.z, qi.z);
+  return fmaf(az, az, fmaf(ay, ay, ax * ax));
+}
+
 // Test the candidates of slot range [lo, hi) (all with image `code`, or 0xff for
-// the per-pair minimum image) against particle li and append the partners.
-// With `sorted`, the range is ordered by x (key: float x in q.w) and only the
-// window xlo <= x_j < xhi can hold partners (|dx| < rl, bounds widened by a
-// margin); the first candidate is found by bisection and the sweep stops at xhi.
+// the per-pair minimum image) against particle li and append the partners, in
+// candidate order. With `sorted`, the range is ordered by x (key: float x in q.w)
+// and only the window xlo <= x_j < xhi can hold partners (|dx| < rl, bounds
+// widened by a margin): the first candidate is found by bisection and the sweep
+// stops past xhi. Candidates are taken four at a time (independent loads,
+// straight-line tests); the rare accepted ones take the slow path in order.
+template <class Out>
 __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const double4_32a* __restrict__ xs,
                                             int lo, int hi, unsigned code, int li, const int4& qi,
-                                            const double4_32a& xi, const LBParams& P, ListOut& o,
+                                            const double4_32a& xi, const LBParams& P, Out& o,
                                             bool sorted, float xlo, float xhi) {
   if (sorted) {
     int b = hi;
@@ -288,27 +336,22 @@ __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const d
       else b = m;
     }
   }
-  int4 qn = lo < hi ? qs[lo] : qi;
-  for (int j = lo; j < hi; ++j) {
-    const int4 qj = qn;
-    if (j + 1 < hi) qn = qs[j + 1];  // issue the next load before this test
-    if (sorted && !(__int_as_float(qj.w) < xhi)) break;
-    const float ax = (float)wrapped_diff(qj.x, qi.x);
-    const float ay = (float)wrapped_diff(qj.y, qi.y);
-    const float az = (float)wrapped_diff(qj.z, qi.z);
-    const float r2q = fmaf(az, az, fmaf(ay, ay, ax * ax));
-    if (!(r2q < P.rl2q_hi) || j == li) continue;
-    unsigned cj = code;
-    bool inside = true;
-    if (!(r2q < P.rl2q_lo) || code == 0xffu) {
-      const double4_32a xj = xs[j];
-      const unsigned r = exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, P.L, P.rl2);
-      cj = r & 0xffu;
-      inside = (r >> 8) & 1u;
-    }
-    if (inside) {
-      if (o.count < o.kmax) o.out[(int64_t)(o.count >> 2) * (4 * kTile) + (o.count & 3)] = (uint32_t)j | (cj << kIdxBits);
-      ++o.count;
+  for (int j = lo; j < hi; j += 4) {
+    const int4 q0 = qs[j];
+    const int4 q1 = j + 1 < hi ? qs[j + 1] : q0;
+    const int4 q2 = j + 2 < hi ? qs[j + 2] : q0;
+    const int4 q3 = j + 3 < hi ? qs[j + 3] : q0;
+    if (sorted && !(__int_as_float(q0.w) < xhi)) break;
+    const float r0 = r2_fixed(q0, qi), r1 = r2_fixed(q1, qi), r2 = r2_fixed(q2, qi), r3 = r2_fixed(q3, qi);
+    unsigned m = (r0 < P.rl2q_hi ? 1u : 0u) | (r1 < P.rl2q_hi ? 2u : 0u) | (r2 < P.rl2q_hi ? 4u : 0u) |
+                 (r3 < P.rl2q_hi ? 8u : 0u);
+    m &= (hi - j) >= 4 ? 15u : ((1u << (hi - j)) - 1u);
+    if ((unsigned)(li - j) < 4u) m &= ~(1u << (li - j));  // not the particle itself
+    if (m) {
+      if (m & 1u) accept(xs, j, r0, code, xi, P, o);
+      if (m & 2u) accept(xs, j + 1, r1, code, xi, P, o);
+      if (m & 4u) accept(xs, j + 2, r2, code, xi, P, o);
+      if (m & 8u) accept(xs, j + 3, r3, code, xi, P, o);
     }
   }
 }
@@ -328,8 +371,11 @@ __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const d
 // the pair is certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only
 // the thin shell between needs the FP64 test. The result is identical to always
 // taking it.
-template <int BLOCK>
+// VAR bit 0: prune rows and narrow x windows by the y / z distance to the row;
+// VAR bit 1: write entries four at a time. Chosen by the autotuner.
+template <int BLOCK, int VAR>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a, int cur) {
+  constexpr bool kPrune = (VAR & 1) != 0;
   const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= a.ntiles) return;
@@ -346,16 +392,22 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
   const double4_32a xi = xs[li];
   const int4 qi = qs[li];
   LBParams P{Pp->L, Pp->rl2, Pp->rl2q_lo, Pp->rl2q_hi, Pp->n};
-  // half-width of the x window: rl plus a margin far above the float rounding
-  // of the keys (about 1e-7 L)
-  const float wpad = (float)(sqrt(Pp->rl2) + 1e-5 * Pp->L + 1e-6);
-  ListOut o{a.nbr + list_word(Pp->l_off, tl, Pp->kmax, lane, 0), 0, Pp->kmax};
+  // Geometric windows: a partner in a row with offsets (oy, oz) is at least
+  // dy_min, dz_min away in y and z (distance of x_i to its cell's faces), so its
+  // x separation is below sqrt(rl^2 - dy_min^2 - dz_min^2); rows where that is
+  // negative are skipped. The margin (1e-5 L) is far above the float rounding of
+  // the keys and of the cell faces (about 1e-7 L).
+  const float rl = Pp->rlf, cs = Pp->csf, wm = Pp->wmargin;
+  ListOut<(VAR & 2) != 0> o{a.nbr + list_word(Pp->l_off, tl, Pp->kmax, lane, 0), 0, Pp->kmax, make_uint4(0, 0, 0, 0)};
   const int nc = Pp->nc;
   const int32_t* cst = a.cstart + Pp->c_off;
   int cx = 0, cy = 0, cz = 0;
+  float fy = 0.f, fz = 0.f;  // offsets of x_i from its cell's lower faces
   if (nc > 1) {
     const int ci = a.cell[p_off + li];
     cx = ci % nc; cy = (ci / nc) % nc; cz = ci / (nc * nc);
+    fy = (float)xi.y - (float)cy * cs;
+    fz = (float)xi.z - (float)cz * cs;
   }
   // 9 rows of the 27-cell block (2 ranges each at most), or one range of all
   // particles when nc == 1
@@ -364,9 +416,18 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
   for (int seg = 0; seg < nseg; ++seg) {
     int lo, hi;
     unsigned code;
+    float w = rl + wm;  // half-width of the x window
     if (nc > 1) {
       const int rowi = seg >> 1, part = seg & 1;
-      int nz = cz + rowi / 3 - 1, ny = cy + rowi % 3 - 1;
+      const int oz = rowi / 3 - 1, oy = rowi % 3 - 1;
+      if (kPrune) {
+        const float dy = fmaxf(0.f, (oy < 0 ? fy : (oy > 0 ? cs - fy : 0.f)) - wm);
+        const float dz = fmaxf(0.f, (oz < 0 ? fz : (oz > 0 ? cs - fz : 0.f)) - wm);
+        const float rem = rl * rl - dy * dy - dz * dz;
+        if (rem <= 0.f) continue;  // the whole row is farther than rl
+        w = sqrtf(rem) + wm;
+      }
+      int nz = cz + oz, ny = cy + oy;
       unsigned shz = 0, shy = 0;
       if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
       if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
@@ -389,11 +450,17 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
     // x window of the candidates in this range's own coordinates
     const float sx = (code & 3u) == 2u ? (float)Pp->L : ((code & 3u) == 1u ? -(float)Pp->L : 0.0f);
     const float xw = (float)xi.x + sx;
-    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o, nc > 1, xw - wpad, xw + wpad);
+    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o, nc > 1, xw - w, xw + w);
   }
+  o.flush();
   a.ncnt[p_off + li] = o.count < o.kmax ? o.count : o.kmax;
-  if (o.count > o.kmax) atomicMax(&a.status[sys].overflow, o.count);
-  atomicMax(&a.status[sys].max_count, o.count);
+  // one atomic per warp (all threads of a system hitting one word serialise)
+  const unsigned act = __activemask();
+  const int wmax = __reduce_max_sync(act, o.count);
+  if (lane == __ffs(act) - 1) {
+    atomicMax(&a.status[sys].max_count, wmax);
+    if (wmax > o.kmax) atomicMax(&a.status[sys].overflow, wmax);
+  }
 }
 
 // ------------------------------------- fused force + velocity-Verlet step
@@ -533,7 +600,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
 #pragma unroll
       for (int u = 0; u < GROUPS; ++u) e[u] = en[u];
     }
-    Fx = fx; Fy = fy; Fz = fz;
+    Fx = f2d_bits(fx); Fy = f2d_bits(fy); Fz = f2d_bits(fz);  // exact, no FP64-pipe conversion
   }
   unsigned long long d2b = 0ull;
   if (t.act) d2b = integrate<true>(a, P, t, cur, xi, Fx, Fy, Fz, ka, kb, flags);
@@ -749,11 +816,21 @@ inline unsigned blocks_of(const DevArrays& a, int block) {
 }
 }  // namespace
 
+template <int VAR>
+static void launch_build_list_v(const DevArrays& a, int cur, int block, cudaStream_t s) {
+  switch (block) {
+    case 64: k_build_list<64, VAR><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
+    case 256: k_build_list<256, VAR><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
+    default: k_build_list<128, VAR><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+  }
+}
+
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s) {
-  switch (tu.list_block) {
-    case 64: k_build_list<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
-    case 256: k_build_list<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
-    default: k_build_list<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+  switch (tu.list_variant) {
+    case 1: launch_build_list_v<1>(a, cur, tu.list_block, s); break;
+    case 2: launch_build_list_v<2>(a, cur, tu.list_block, s); break;
+    case 3: launch_build_list_v<3>(a, cur, tu.list_block, s); break;
+    default: launch_build_list_v<0>(a, cur, tu.list_block, s); break;
   }
 }
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,

@@ -24,8 +24,22 @@ static __device__ __forceinline__ double wrap_fast(double x, double L) {
   return x;
 }
 
+// floor(y) for 0 <= y < 2^31 by integer operations on the bits (negative y
+// gives -1, NaN gives 0x7fffffff; callers clamp).
+static __device__ __forceinline__ int floor_bits(double y) {
+  const long long b = __double_as_longlong(y);
+  if (b < 0) return -1;
+  const int ef = (int)(b >> 52);
+  if (ef < 1023) return 0;                      // 0 <= y < 1
+  if (ef > 1023 + 30) return 0x7fffffff;        // too large (or inf / NaN)
+  const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  return (int)(m >> (1075 - ef));
+}
+
+// Cell index along one axis: min(floor(x * nc / L), nc - 1), the product rounded
+// once in FP64 exactly as the reference computes it, the floor on the bits.
 static __device__ __forceinline__ int cell_axis(double x, double inv_cs, int nc) {
-  int k = (int)floor(__dmul_rn(x, inv_cs));
+  int k = floor_bits(__dmul_rn(x, inv_cs));
   if (k > nc - 1) k = nc - 1;
   if (k < 0) k = 0;
   return k;
@@ -35,10 +49,41 @@ static __device__ __forceinline__ int cell_of(const double4_32a& x, double inv_c
   return cell_axis(x.x, inv_cs, nc) + nc * (cell_axis(x.y, inv_cs, nc) + nc * cell_axis(x.z, inv_cs, nc));
 }
 
+// Round a double to the nearest integer (ties to even) and keep the low 32 bits,
+// with integer operations only (no FP64-pipe conversion). Same result as
+// (int)(unsigned)__double2ll_rn(y) for |y| < 2^62.
+static __device__ __forceinline__ int round_low32(double y) {
+  const long long b = __double_as_longlong(y);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  if (ef < 1022) return 0;  // |y| < 0.5 (or zero / subnormal)
+  const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int shift = 1075 - ef;  // y = m 2^-shift
+  unsigned long long r;
+  if (shift <= 0) {
+    r = m << (-shift);
+  } else {
+    r = m >> shift;
+    const unsigned long long rem = m & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+    if (rem > half || (rem == half && (r & 1ull))) ++r;
+  }
+  if (b < 0) r = 0ull - r;
+  return (int)(unsigned)r;
+}
+
 // Fixed-point shadow coordinate: round(x 2^32 / L) mod 2^32. Differences of two
 // such values, taken as wrapped 32-bit integers, are minimum-image separations.
 static __device__ __forceinline__ int to_fixed(double x, double qscale) {
-  return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
+  return round_low32(x * qscale);
+}
+
+// Exact float -> double with integer operations (subnormal floats become zero).
+static __device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned fb = __float_as_uint(f);
+  const unsigned ex = (fb >> 23) & 0xFFu;
+  const unsigned sign = fb & 0x80000000u;
+  if (ex == 0u) return __longlong_as_double((long long)sign << 32);
+  const unsigned hi = sign | ((ex == 0xFFu ? 0x7FFu : ex + 896u) << 20) | ((fb & 0x7FFFFFu) >> 3);
+  return __longlong_as_double(((long long)hi << 32) | ((long long)(fb & 7u) << 29));
 }
 
 static __device__ __forceinline__ int4 fixed4(const double4_32a& x, double qscale) {

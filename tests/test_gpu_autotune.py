@@ -13,9 +13,9 @@ def test_tuning_does_not_change_results(ljmd, precision):
     x, box = li.perturbed_fcc(3000, 0.8442, 0.08, 501)
     v = li.maxwell_boltzmann(3000, 0.9, 502)
     outs = []
-    for tun in [dict(step_block=128, step_groups=1, list_block=128),
-                dict(step_block=64, step_groups=2, list_block=256),
-                dict(step_block=256, step_groups=2, list_block=64)]:
+    for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=0),
+                dict(step_block=64, step_groups=2, list_block=256, list_variant=3),
+                dict(step_block=256, step_groups=2, list_block=64, list_variant=1)]:
         with ljmd.LJSystem(box, 3000, 2.5, 0.3, precision) as s:
             s.set_tuning(**tun)
             assert s.get_tuning() == tun
