@@ -56,6 +56,15 @@ extern "C" {
 #define MD_FP64 0       /* all pair arithmetic in FP64                                   */
 #define MD_FP32_FORCE 1 /* pair forces in FP32 from fixed-point separations; positions,  */
                         /* velocities, list distance tests, energies, virial stay FP64  */
+/* FP64 forms whose r^-8 and r^-14 come from an approximate reciprocal y of r^2, as in the
+ * paper's FX10 kernel (Sec. 3.3): y is r^2's float reciprocal with its mantissa cut to 8
+ * bits (the stand-in for SPARC64 frcpad, relative error < 1/256, Eq. 2) or kept (23 bits);
+ * the _CORR forms apply Eqs. 2-7: r^-8 ~ y^4 (5 - 4 y r^2), r^-14 ~ y^7 (8 - 7 y r^2). Energies
+ * and the virial stay exact FP64. */
+#define MD_FP64_RCP8 2
+#define MD_FP64_RCP8_CORR 3
+#define MD_FP64_RCP23 4
+#define MD_FP64_RCP23_CORR 5
 
 /* Largest particle count of one system (the list packs a slot index in 26 bits). */
 #define MD_MAX_N ((int64_t)((1 << 26) - 1))
@@ -71,7 +80,8 @@ typedef struct md_ctx md_ctx;
  * Errors: MD_ERR_ARG, MD_ERR_OOM, MD_ERR_CUDA. */
 MD_API int md_create(double box_L, int64_t N, double rc, double skin, md_ctx** out);
 
-/* Select MD_FP64 or MD_FP32_FORCE. Cached forces are invalidated. */
+/* Select the force form (MD_FP64, MD_FP32_FORCE, MD_FP64_RCP*). Cached forces are
+ * invalidated. */
 MD_API int md_set_precision(md_ctx* ctx, int mode);
 
 /* Copy positions x (N*3, any real values: wrapped into [0, L) on entry) and velocities
@@ -260,6 +270,10 @@ MD_API int md_batch_forces(md_batch* b, int id, double* f);
 /* Observables of every active system: out[5 * id + {0..4}] = pe, virial, ke, T, P
  * (as md_observables); out holds 5 * max_systems doubles (inactive ids get zeros). */
 MD_API int md_batch_observables(md_batch* b, double* out);
+
+/* Same for the systems with select[id] != 0 only (select: max_systems int32); the
+ * other entries of out are zero. Costs in proportion to the selected systems. */
+MD_API int md_batch_observables_select(md_batch* b, const int32_t* select, double* out);
 
 /* Kinetic energy of every active system: ke[id] (max_systems doubles, 0 if inactive). */
 MD_API int md_batch_kinetic_energy(md_batch* b, double* ke);

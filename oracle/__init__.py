@@ -46,6 +46,10 @@ def _load():
             "orc_forces_brute": (None, [_I64, _D, _D, _D, _PD, _PD]),
             "orc_observables_list": (None, [_I64, _D, _D, _D, _D, _PD, _PD, _PI64, _PI32, _PD]),
             "orc_run": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64]),
+            "orc_run_mode": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64,
+                                       C.c_int, C.c_int]),
+            "orc_pair_force_factor_rcp": (_D, [_D, _D, _D, C.c_int, C.c_int]),
+            "orc_forces_list_rcp": (None, [_I64, _D, _D, _D, _PD, _PI64, _PI32, C.c_int, C.c_int, _PD]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -130,6 +134,22 @@ def forces_list(x, box: float, rc: float, c2: float, start, partners) -> np.ndar
     return f
 
 
+def pair_force_factor_rcp(r2: float, rc: float, c2: float, bits: int, corr: bool) -> float:
+    """Force factor with r^-8, r^-14 from an approximate reciprocal of r^2 (Sec. 3.3,
+    Eqs. 2-7): `bits` mantissa bits kept (8: relative error < 1/256), corrected or not."""
+    return _load().orc_pair_force_factor_rcp(r2, rc * rc, c2, int(bits), 1 if corr else 0)
+
+
+def forces_rcp(x, box: float, rc: float, bits: int, corr: bool, skin: float = 0.3) -> np.ndarray:
+    c2 = lj_coeffs(rc)[0]
+    x = _f64(x, (-1, 3))
+    start, partners = build_list(x, box, rc + skin)
+    f = np.empty_like(x)
+    _load().orc_forces_list_rcp(x.shape[0], box, rc, c2, _pd(x), start.ctypes.data_as(_PI64),
+                                partners.ctypes.data_as(_PI32), int(bits), 1 if corr else 0, _pd(f))
+    return f
+
+
 def forces(x, box: float, rc: float, skin: float = 0.3, c2: float | None = None) -> np.ndarray:
     """Forces through the cell-built list (list radius rc + skin)."""
     if c2 is None:
@@ -172,8 +192,9 @@ def observables(x, v, box: float, rc: float, skin: float = 0.3, c2=None, c0=None
 
 
 def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
-        trace_every: int = 0) -> dict:
-    """Velocity-Verlet run; returns dict(x, v, rebuilds, trace)."""
+        trace_every: int = 0, rcp_bits: int = -1, rcp_corr: bool = False) -> dict:
+    """Velocity-Verlet run; returns dict(x, v, rebuilds, trace). With rcp_bits >= 0 the
+    forces use the approximate-reciprocal factor of Sec. 3.3."""
     x = _f64(x, (-1, 3)).copy()
     v = _f64(v, (-1, 3)).copy()
     rebuilds = _I64(0)
@@ -182,8 +203,8 @@ def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
     if trace_every > 0:
         trace = np.empty(1 + nsteps // trace_every)
         tp = _pd(trace)
-    rc_ = _load().orc_run(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt,
-                          C.byref(rebuilds), tp, trace_every)
+    rc_ = _load().orc_run_mode(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt,
+                               C.byref(rebuilds), tp, trace_every, int(rcp_bits), 1 if rcp_corr else 0)
     if rc_ != 0:
         raise MemoryError("oracle run failed to allocate")
     return dict(x=x, v=v, rebuilds=rebuilds.value, trace=trace)

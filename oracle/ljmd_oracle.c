@@ -75,6 +75,42 @@ ORC_API double orc_pair_virial(double r2, double rc2, double c2) {
     return 48.0 * ir6 * ir6 - 24.0 * ir6 - 8.0 * c2 * r2;
 }
 
+/* ------------------------------------ reciprocal approximation (Sec. 3.3) */
+
+/* Approximate reciprocal of r^2 standing in for SPARC64 frcpad: r^2 rounded to
+ * float, its correctly rounded float reciprocal, the mantissa truncated to
+ * `bits` bits (bits = 8 gives a relative error below 1/256 as Eq. 2 states;
+ * bits >= 23 keeps the float value). */
+static double approx_rcp(double r2, int bits) {
+    float f = (float)r2;
+    float y = 1.0f / f;
+    if (bits < 23) {
+        uint32_t u;
+        memcpy(&u, &y, sizeof(u));
+        u &= ~((1u << (23 - bits)) - 1u);
+        memcpy(&y, &u, sizeof(u));
+    }
+    return (double)y;
+}
+
+/* Force factor of Algorithm 1 with r^-8 and r^-14 built from the approximate
+ * reciprocal y of r^2 (Sec. 3.3): uncorrected y^4 and y^7, or corrected by
+ * Eqs. 2-7: r^-8 ~ y^4 (5 - 4 y r^2), r^-14 ~ y^7 (8 - 7 y r^2). */
+ORC_API double orc_pair_force_factor_rcp(double r2, double rc2, double c2, int bits, int corr) {
+    if (!(r2 < rc2)) return 0.0;
+    double y = approx_rcp(r2, bits);
+    double y2 = y * y;
+    double y4 = y2 * y2;
+    double y7 = y4 * y2 * y;
+    double ir8 = y4, ir14 = y7;
+    if (corr) {
+        double e = y * r2;
+        ir8 = y4 * (5.0 - 4.0 * e);
+        ir14 = y7 * (8.0 - 7.0 * e);
+    }
+    return 24.0 * ir8 - 48.0 * ir14 + 8.0 * c2;
+}
+
 /* ------------------------------------------------------- periodic box */
 
 /* Minimum image of one separation component: d - L * nearbyint(d / L). */
@@ -230,6 +266,27 @@ ORC_API void orc_forces_list(int64_t n, double box, double rc, double c2, const 
     }
 }
 
+/* Forces over the list with the approximate-reciprocal force factor. */
+ORC_API void orc_forces_list_rcp(int64_t n, double box, double rc, double c2, const double* x,
+                                 const int64_t* start, const int32_t* partners, int bits, int corr,
+                                 double* f) {
+    double rc2 = rc * rc;
+    for (int64_t i = 0; i < n; ++i) {
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+            double dx, dy, dz;
+            double r2 = dist2(x, i, partners[k], box, &dx, &dy, &dz);
+            double g = orc_pair_force_factor_rcp(r2, rc2, c2, bits, corr);
+            fx += g * dx;
+            fy += g * dy;
+            fz += g * dz;
+        }
+        f[3 * i + 0] = fx;
+        f[3 * i + 1] = fy;
+        f[3 * i + 2] = fz;
+    }
+}
+
 /* Force on particle i by direct summation over all j != i (no list), j ascending. */
 ORC_API void orc_force_on(int64_t n, double box, double rc, double c2, const double* x,
                           int64_t i, double* f3) {
@@ -331,9 +388,29 @@ static double max_displacement(const orc_list_state* s, const double* x) {
  * trace_every steps (1 + nsteps / trace_every entries).
  * Returns 0, or -1 on allocation failure. *rebuilds gets the number of builds
  * (including the initial one). */
+static void forces_mode(const orc_list_state* s, const double* x, int rcp_bits, int rcp_corr,
+                        double* f) {
+    if (rcp_bits < 0)
+        orc_forces_list(s->n, s->box, s->rc, s->c2, x, s->start, s->partners, f);
+    else
+        orc_forces_list_rcp(s->n, s->box, s->rc, s->c2, x, s->start, s->partners, rcp_bits,
+                            rcp_corr, f);
+}
+
+/* As orc_run, with the approximate-reciprocal force factor when rcp_bits >= 0. */
+ORC_API int orc_run_mode(int64_t n, double box, double rc, double skin, double* x, double* v,
+                         int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
+                         int64_t trace_every, int rcp_bits, int rcp_corr);
+
 ORC_API int orc_run(int64_t n, double box, double rc, double skin, double* x, double* v,
                     int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
                     int64_t trace_every) {
+    return orc_run_mode(n, box, rc, skin, x, v, nsteps, dt, rebuilds, trace, trace_every, -1, 0);
+}
+
+ORC_API int orc_run_mode(int64_t n, double box, double rc, double skin, double* x, double* v,
+                         int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
+                         int64_t trace_every, int rcp_bits, int rcp_corr) {
     orc_list_state s;
     memset(&s, 0, sizeof(s));
     s.n = n;
@@ -351,7 +428,7 @@ ORC_API int orc_run(int64_t n, double box, double rc, double skin, double* x, do
     if (!s.partners || !s.start || !s.x_ref || !f) { rc_ = -1; goto done; }
     orc_wrap(n, box, x);
     if (list_rebuild(&s, x)) { rc_ = -1; goto done; }
-    orc_forces_list(n, box, rc, s.c2, x, s.start, s.partners, f);
+    forces_mode(&s, x, rcp_bits, rcp_corr, f);
     double hdt = 0.5 * dt;
     int64_t ti = 0;
     if (trace) {
@@ -365,7 +442,7 @@ ORC_API int orc_run(int64_t n, double box, double rc, double skin, double* x, do
         if (2.0 * max_displacement(&s, x) >= skin) {
             if (list_rebuild(&s, x)) { rc_ = -1; goto done; }
         }
-        orc_forces_list(n, box, rc, s.c2, x, s.start, s.partners, f);
+        forces_mode(&s, x, rcp_bits, rcp_corr, f);
         for (int64_t k = 0; k < 3 * n; ++k) v[k] = v[k] + hdt * f[k];
         if (trace && trace_every > 0 && step % trace_every == 0) {
             double o[5];

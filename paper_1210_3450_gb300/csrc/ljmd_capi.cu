@@ -532,7 +532,7 @@ int md_batch_forces(md_batch* b, int id, double* f) {
   return bd2h(b, f, st, 3 * n);
 }
 
-int md_batch_observables(md_batch* b, double* out) {
+int md_batch_observables_select(md_batch* b, const int32_t* select, double* out) {
   int r = check_batch(b);
   if (r) return r;
   if (!out) {
@@ -541,11 +541,11 @@ int md_batch_observables(md_batch* b, double* out) {
   }
   const int ns = b->eng.nsys();
   std::vector<double> o3((size_t)(3 * ns));
-  if ((r = b->eng.observables(o3.data(), b->stream))) return r;
+  if ((r = b->eng.observables(o3.data(), b->stream, true, select))) return r;
   for (int k = 0; k < ns; ++k) {
     double* q = out + 5 * k;
     const ljmd::SysHost& h = b->eng.sys(k);
-    if (!h.used || !h.active) {
+    if (!h.used || !h.active || (select && !select[k])) {
       for (int m = 0; m < 5; ++m) q[m] = 0.0;
       continue;
     }
@@ -587,6 +587,8 @@ int md_batch_scale_velocities(md_batch* b, const double* factor) {
   std::vector<double> f(factor, factor + b->eng.nsys());
   return b->eng.scale_velocities(f, b->stream);
 }
+
+int md_batch_observables(md_batch* b, double* out) { return md_batch_observables_select(b, nullptr, out); }
 
 int md_batch_stats(md_batch* b, int id, int64_t* rebuilds, int64_t* steps) {
   int r = check_batch(b);

@@ -122,14 +122,18 @@ void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, 
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
+// mode 0: FP64 reciprocal; 1..4: approximate reciprocal of Sec. 3.3 (8 bits,
+// 8 bits corrected, 23 bits, 23 bits corrected)
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
-                      cudaStream_t s);
+                      int mode, cudaStream_t s);
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s);
-void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, cudaStream_t s);
+// select: per-system flags (NULL = every active system)
+void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, const int32_t* select, cudaStream_t s);
 void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s);
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s);
-void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, cudaStream_t s);
+void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, const int32_t* select,
+                       cudaStream_t s);
 void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n,
                       int sys, int64_t ntiles_sys, cudaStream_t s);
 void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v,

@@ -296,7 +296,7 @@ int Engine::init(const std::vector<SysSpec>& specs, int precision) {
 }
 
 int Engine::init_arena(const ArenaCaps& caps, int precision) {
-  if (precision != 0 && precision != 1) { set_error("unknown precision mode"); return kErrArg; }
+  if (precision < 0 || precision > 5) { set_error("unknown precision mode"); return kErrArg; }
   if (caps.slots <= 0 || caps.cells <= 0 || caps.list_words <= 0 || caps.max_systems <= 0) {
     set_error("arena capacities must be positive");
     return kErrArg;
@@ -527,7 +527,7 @@ DevArrays Engine::arrays() const {
 }
 
 int Engine::set_precision(int mode) {
-  if (mode != 0 && mode != 1) { set_error("unknown precision mode"); return kErrArg; }
+  if (mode < 0 || mode > 5) { set_error("unknown precision mode"); return kErrArg; }
   if (mode != precision_) {
     precision_ = mode;
     for (SysHost& h : sys_) {
@@ -667,7 +667,7 @@ int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
   const DevArrays a = arrays();
   tmark_begin(kTStep, s);
   if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
-  else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, s);
+  else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, precision_ >= 2 ? precision_ - 1 : 0, s);
   tmark_end(s);
   CKL();
   n_launch_ += 1;
@@ -767,11 +767,18 @@ int Engine::forces_dev(int k, double* f, cudaStream_t s) {
   return kOK;
 }
 
-int Engine::observables(double* out3, cudaStream_t s, bool with_pairs) {
+int Engine::observables(double* out3, cudaStream_t s, bool with_pairs, const int32_t* select) {
   if (with_pairs) CKR(ensure_lists(s));
   const DevArrays a = arrays();
-  launch_pe_virial(a, cur_, with_pairs ? 1 : 0, s);
-  launch_reduce_obs(a, cur_, nsys(), d_obs_, s);
+  const int32_t* dsel = nullptr;
+  if (select) {
+    // the selection rides in the rebuild-flag array (not in use between steps)
+    for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = select[k] ? 1 : 0;
+    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * nsys(), cudaMemcpyHostToDevice, s));
+    dsel = d_rebuild_;
+  }
+  launch_pe_virial(a, cur_, with_pairs ? 1 : 0, dsel, s);
+  launch_reduce_obs(a, cur_, nsys(), d_obs_, dsel, s);
   CKL();
   CK(cudaMemcpyAsync(h_obs_, d_obs_, sizeof(double) * 3 * nsys(), cudaMemcpyDeviceToHost, s));
   CKR(sync_check(s));

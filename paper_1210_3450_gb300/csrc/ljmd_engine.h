@@ -109,7 +109,9 @@ class Engine {
   // entries of inactive ids are ignored).
   int step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s);
   // Observables (pe, virial, ke) of every active system into host out3[3 * nsys].
-  int observables(double* out3, cudaStream_t s, bool with_pairs = true);
+  // select: nsys flags choosing the systems (NULL = every active system); the
+  // entries of unselected systems in out3 are unspecified.
+  int observables(double* out3, cudaStream_t s, bool with_pairs = true, const int32_t* select = nullptr);
   // v *= factor[id] for every active system (factor: nsys doubles).
   int scale_velocities(const std::vector<double>& factor, cudaStream_t s);
   // Rebuild the lists of all active systems now.

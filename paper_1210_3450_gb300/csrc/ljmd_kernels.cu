@@ -611,7 +611,42 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
 // pair inside rc the reciprocal (3 DFMA after an integer-built FP32 seed),
 // powers (3), factor (2) and accumulation (3). The cutoff test compares bit
 // patterns (r^2 >= 0), so it costs no FP64 instruction.
-template <int BLOCK>
+// Approximate reciprocal of r^2 for the force variants of Sec. 3.3: r^2 rounded
+// to float, its correctly rounded float reciprocal, the mantissa cut to 8 bits
+// for the stand-in of SPARC64 frcpad (relative error < 1/256, Eq. 2).
+template <int BITS>
+__device__ __forceinline__ double approx_rcp(double r2) {
+  float y = __frcp_rn(__double2float_rn(r2));
+  if (BITS < 23) y = __uint_as_float(__float_as_uint(y) & ~((1u << (23 - BITS)) - 1u));
+  return (double)y;
+}
+
+// Force factor g(r) = 24 r^-8 - 48 r^-14 + 8 c2 for MODE 0 (full FP64 reciprocal)
+// or from the approximate reciprocal y: MODE 1 / 3 uncorrected (y^4, y^7) with 8 /
+// 23 bits, MODE 2 / 4 corrected by Eqs. 2-7 (y^4 (5 - 4 y r^2), y^7 (8 - 7 y r^2)).
+template <int MODE>
+__device__ __forceinline__ double force_factor(double r2, double c2x8) {
+  if (MODE == 0) {
+    const double ir2 = rcp_f64(r2);
+    const double ir4 = ir2 * ir2;
+    const double ir6 = ir4 * ir2;
+    const double ir8 = ir4 * ir4;
+    return fma(ir8, fma(-48.0, ir6, 24.0), c2x8);
+  }
+  const double y = approx_rcp<(MODE <= 2) ? 8 : 23>(r2);
+  const double y2 = y * y;
+  const double y4 = y2 * y2;
+  const double y7 = y4 * y2 * y;
+  double ir8 = y4, ir14 = y7;
+  if (MODE == 2 || MODE == 4) {
+    const double e = y * r2;
+    ir8 = y4 * fma(-4.0, e, 5.0);
+    ir14 = y7 * fma(-7.0, e, 8.0);
+  }
+  return fma(24.0, ir8, fma(-48.0, ir14, c2x8));
+}
+
+template <int BLOCK, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
   TileCtx t;
   SysParams P;
@@ -643,11 +678,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
       }
       const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
       if (__double_as_longlong(r2) < rc2b) {
-        const double ir2 = rcp_f64(r2);
-        const double ir4 = ir2 * ir2;
-        const double ir6 = ir4 * ir2;
-        const double ir8 = ir4 * ir4;
-        const double g = fma(ir8, fma(-48.0, ir6, 24.0), c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+        const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
         Fx = fma(g, dx, Fx);
         Fy = fma(g, dy, Fy);
         Fz = fma(g, dz, Fz);
@@ -664,10 +695,12 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
 // Per particle: 1/2 sum_j V(r) and 1/2 sum_j -r V'(r) over listed partners with
 // r < rc (the full list counts each pair twice), and 1/2 |v|^2; each tile sums
 // its 32 values in a fixed shuffle order into tile_obs[3 t ...].
-__global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs) {
+__global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs,
+                                                      const int32_t* __restrict__ select) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
+  if (select && !select[t.sys]) return;
   const int lane = threadIdx.x & 31;
   double pe = 0.0, w = 0.0, ke = 0.0;
   if (t.act && with_pairs) {
@@ -743,11 +776,12 @@ __global__ void __launch_bounds__(kBlock) k_pair_stats(DevArrays a, int cur, uns
 }
 
 // One block per system: fixed-order sum of its tile partials (deterministic).
-__global__ void __launch_bounds__(256) k_reduce_obs(DevArrays a, int nsys, double* out3) {
+__global__ void __launch_bounds__(256) k_reduce_obs(DevArrays a, int nsys, double* out3,
+                                                   const int32_t* __restrict__ select) {
   const int sys = blockIdx.x;
   if (sys >= nsys) return;
   const SysParams P = a.params[sys];
-  if (!P.active) return;
+  if (!P.active || (select && !select[sys])) return;
   __shared__ double sh[3][256];
   double pe = 0.0, w = 0.0, ke = 0.0;
   for (int q = threadIdx.x; q < P.ntiles; q += blockDim.x) {
@@ -833,12 +867,24 @@ void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream
     default: launch_build_list_v<0>(a, cur, tu.list_block, s); break;
   }
 }
+template <int MODE>
+static void launch_step_fp64_m(const DevArrays& a, int cur, double ka, double kb, int flags, int block,
+                               cudaStream_t s) {
+  switch (block) {
+    case 64: k_step_fp64<64, MODE><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, ka, kb, flags); break;
+    case 256: k_step_fp64<256, MODE><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, ka, kb, flags); break;
+    default: k_step_fp64<128, MODE><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, ka, kb, flags); break;
+  }
+}
+
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
-                      cudaStream_t s) {
-  switch (tu.step_block) {
-    case 64: k_step_fp64<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, ka, kb, flags); break;
-    case 256: k_step_fp64<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, ka, kb, flags); break;
-    default: k_step_fp64<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, ka, kb, flags); break;
+                      int mode, cudaStream_t s) {
+  switch (mode) {
+    case 1: launch_step_fp64_m<1>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 2: launch_step_fp64_m<2>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 3: launch_step_fp64_m<3>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 4: launch_step_fp64_m<4>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    default: launch_step_fp64_m<0>(a, cur, ka, kb, flags, tu.step_block, s); break;
   }
 }
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
@@ -856,8 +902,8 @@ void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int fla
   }
 #undef LJMD_STEP32
 }
-void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, cudaStream_t s) {
-  k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, with_pairs);
+void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, const int32_t* select, cudaStream_t s) {
+  k_pe_virial<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, with_pairs, select);
 }
 
 // v *= factor for every particle of the systems with scale[sys] != 1.
@@ -880,8 +926,8 @@ void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s) {
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s) {
   k_pair_stats<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, out2);
 }
-void launch_reduce_obs(const DevArrays& a, int, int nsys, double* out3, cudaStream_t s) {
-  k_reduce_obs<<<nsys, 256, 0, s>>>(a, nsys, out3);
+void launch_reduce_obs(const DevArrays& a, int, int nsys, double* out3, const int32_t* select, cudaStream_t s) {
+  k_reduce_obs<<<nsys, 256, 0, s>>>(a, nsys, out3, select);
 }
 
 }  // namespace ljmd

@@ -24,6 +24,10 @@ MD_ERR_CUDA = -6
 MD_ERR_STATE = -7
 MD_FP64 = 0
 MD_FP32_FORCE = 1
+MD_FP64_RCP8 = 2
+MD_FP64_RCP8_CORR = 3
+MD_FP64_RCP23 = 4
+MD_FP64_RCP23_CORR = 5
 MD_MAX_N = (1 << 26) - 1
 MD_TUNE_STEP_BLOCK = 0
 MD_TUNE_STEP_GROUPS = 1
@@ -92,6 +96,7 @@ SIGNATURES = {
     "md_batch_step_async": (C.c_int, [_P, C.c_int64, _PD, _P]),
     "md_batch_forces": (C.c_int, [_P, C.c_int, _PD]),
     "md_batch_observables": (C.c_int, [_P, _PD]),
+    "md_batch_observables_select": (C.c_int, [_P, _PI32, _PD]),
     "md_batch_stats": (C.c_int, [_P, C.c_int, _PI64, _PI64]),
     "md_batch_set_timing": (C.c_int, [_P, C.c_int]),
     "md_batch_get_timing": (C.c_int, [_P, _PD]),
@@ -418,10 +423,16 @@ class LJBatch:
         _check(_lib.md_batch_forces(self._h, int(sid), _pd(f)))
         return f
 
-    def observables(self) -> np.ndarray:
-        """(max_systems, 5): pe, virial, ke, T, P per id."""
+    def observables(self, select=None) -> np.ndarray:
+        """(max_systems, 5): pe, virial, ke, T, P per id (only the ids in `select`
+        when given; other rows are zero)."""
         out = np.zeros((self.max_systems, 5))
-        _check(_lib.md_batch_observables(self._h, _pd(out)))
+        if select is None:
+            _check(_lib.md_batch_observables(self._h, _pd(out)))
+        else:
+            sel = np.zeros(self.max_systems, dtype=np.int32)
+            sel[list(select)] = 1
+            _check(_lib.md_batch_observables_select(self._h, sel.ctypes.data_as(_PI32), _pd(out)))
         return out
 
     def stats(self, sid: int) -> dict:

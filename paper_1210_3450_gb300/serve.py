@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import collections
+import concurrent.futures as cf
 import json
 import math
 import os
@@ -83,7 +84,8 @@ class MDServer:
     """Admit, step and retire LJ runs in one arena. ``clock`` returns seconds."""
 
     def __init__(self, budget_bytes: int, precision: int = ljmd.MD_FP32_FORCE, chunk: int = 100,
-                 max_systems: int = 4096, keep_state: bool = False, clock=time.perf_counter):
+                 max_systems: int = 4096, keep_state: bool = False, clock=time.perf_counter,
+                 prepare_threads: int = 4):
         self.arena = arena_for_budget(budget_bytes, max_systems)
         self.batch = ljmd.LJBatch(arena=self.arena, precision=precision)
         self.chunk = int(chunk)
@@ -94,9 +96,14 @@ class MDServer:
         self.done: list[Request] = []
         self.particle_steps = 0
         self.gpu_busy = 0.0
+        # initial states are generated on host threads as requests arrive, so that
+        # admission only copies them to the device
+        self.pool = cf.ThreadPoolExecutor(max_workers=prepare_threads)
+        self.prepared: dict[int, cf.Future] = {}
         self.t0 = self.clock()  # times of requests are seconds since t0
 
     def close(self):
+        self.pool.shutdown(wait=False, cancel_futures=True)
         self.batch.close()
 
     def fits_ever(self, r: Request) -> bool:
@@ -106,6 +113,13 @@ class MDServer:
 
     def submit(self, r: Request):
         self.pending.append(r)
+        self._prepare_ahead()
+
+    def _prepare_ahead(self, depth: int = 32):
+        """Start generating the states of the first `depth` pending requests."""
+        for r in list(self.pending)[:depth]:
+            if id(r) not in self.prepared:
+                self.prepared[id(r)] = self.pool.submit(initial_state, r)
 
     def admit(self, now: float, backfill: int = 64):
         """FIFO admission; up to `backfill` later requests may pass a head that does
@@ -118,13 +132,15 @@ class MDServer:
                 if skipped > backfill:
                     break
                 continue
-            x, v = initial_state(r)
+            fut = self.prepared.pop(id(r), None)
+            x, v = fut.result() if fut is not None else initial_state(r)
             self.batch.set_state(sid, x, v)
             r.sid = sid
             r.admitted = now
             r.remaining = r.steps
             self.running[sid] = r
             self.pending.remove(r)
+        self._prepare_ahead()
 
     def step_chunk(self) -> int:
         if not self.running:
@@ -141,7 +157,7 @@ class MDServer:
             if r.remaining == 0:
                 finished.append(sid)
         if finished:
-            obs = self.batch.observables()
+            obs = self.batch.observables(select=finished)
             now = self.clock() - self.t0
             for sid in finished:
                 r = self.running.pop(sid)

@@ -353,3 +353,47 @@ def test_cavitation_expansion_density():
     with open(os.path.join(GOLDEN, "paper_benchmark_tables.json")) as fh:
         c = json.load(fh)["cavitation"]
     assert c["density_before"] / c["rescale_factor"] ** 3 == pytest.approx(c["density_after"], abs=5e-3)
+
+
+# ------------------------------------- reciprocal approximation (Sec. 3.3)
+
+@pytest.mark.parametrize("bits", [8, 12, 23])
+def test_reciprocal_approximation_error_orders(oracle, bits):
+    """Eqs. 2-7: with r~^-2 = r^-2 (1 + eps), |eps| < 2^-bits, the uncorrected
+    powers err by n eps (first order) and the corrected ones y^4 (5 - 4 y r^2),
+    y^7 (8 - 7 y r^2) by 10 eps^2 and 28 eps^2 (second order, from the Taylor
+    expansions (1+e)^4 (1-4e) = 1 - 10 e^2 + ..., (1+e)^7 (1-7e) = 1 - 28 e^2 + ...)."""
+    rc = 2.5
+    c2, _ = oracle.lj_coeffs(rc)
+    eps = 2.0 ** -bits
+    for r in np.linspace(0.85, 2.49, 400):
+        r2 = r * r
+        ir8, ir14 = r ** -8, r ** -14
+        ex = oracle.pair_force_factor(r2, rc, c2)
+        unc = oracle.pair_force_factor_rcp(r2, rc, c2, bits, False)
+        cor = oracle.pair_force_factor_rcp(r2, rc, c2, bits, True)
+        # float rounding of r^2 and of its reciprocal add 2^-24 each to eps
+        e = eps + 2.0 ** -23
+        bound1 = (24 * 4 * ir8 + 48 * 7 * ir14) * e * 1.05 + 1e-13 * (24 * ir8 + 48 * ir14)
+        bound2 = (24 * 10 * ir8 + 48 * 28 * ir14) * e * e * 1.05 + 1e-13 * (24 * ir8 + 48 * ir14)
+        assert abs(unc - ex) <= bound1
+        assert abs(cor - ex) <= bound2
+        if bits <= 12:
+            assert abs(cor - ex) <= abs(unc - ex)
+
+
+def test_reciprocal_approximation_eight_bits_below_1_256(oracle):
+    """The 8-bit stand-in for frcpad meets Eq. 2: |(y - 1/x) / (1/x)| < 1/256."""
+    c2, _ = oracle.lj_coeffs(2.5)
+    for r in np.linspace(0.8, 2.49, 997):
+        r2 = r * r
+        # untruncated force factor -> y^4, y^7 only differ through y: recover the
+        # relative error of y from the uncorrected r^-8 term at c2 = 0
+        g = oracle.pair_force_factor_rcp(r2, 100.0, 0.0, 8, False)   # 24 y^4 - 48 y^7
+        y_exact = 1.0 / r2
+        # solve 24 y^4 - 48 y^7 = g for y near y_exact by Newton
+        y = y_exact
+        for _ in range(50):
+            fval = 24 * y ** 4 - 48 * y ** 7 - g
+            y -= fval / (96 * y ** 3 - 336 * y ** 6)
+        assert abs(y - y_exact) / y_exact < 1.0 / 256.0
