@@ -45,6 +45,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--skip-cpu-baseline", action="store_true")
+    p.add_argument("--skip-batched", action="store_true", help="no batched-replica / serving sub-results")
+    p.add_argument("--serve-seconds", type=float, default=20.0)
     return p.parse_args()
 
 
@@ -265,6 +267,13 @@ def run_ours(args):
     e2e = e2e_run(ljmd, cfg, ljmd.MD_FP32_FORCE, args.steps)
     e2e_val = world * cfg.n * args.steps / e2e["seconds"]
 
+    batched = serve = None
+    if not args.skip_batched and rank == 0:
+        from paper_1210_3450_gb300 import workloads
+        batched = workloads.batched(count=256, steps=500, warmup=10)
+        rate = 0.8 * batched["value"] / workloads.mean_request_work()
+        serve = workloads.serve_run(rate, args.serve_seconds, budget_gb=100.0)
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -320,6 +329,13 @@ def run_ours(args):
                 "note": "set_state (host x, v) + steps + get_state + observables through the C ABI, wall clock"},
         "clocks": ck,
     }
+    if batched:
+        line["batched"] = {k: batched[k] for k in ("workload", "value", "unit", "ms_per_step", "steps",
+                                                    "list_builds", "launches_per_step")}
+    if serve:
+        line["serve"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in serve.items()}
+        line["serve"]["note"] = ("Poisson arrivals at 80% of the batched capacity, N log-uniform "
+                                 "[1e3, 1e6], steps [1e3, 1e4]; latency includes queueing")
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

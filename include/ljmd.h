@@ -147,6 +147,16 @@ MD_API int md_list_size(md_ctx* ctx, int64_t* total);
  * in the library's internal order per particle (sort to compare as sets). */
 MD_API int md_get_list(md_ctx* ctx, int64_t* start, int32_t* partners);
 
+/* Bubble identification (Sec. 4.2): particles are counted in ns^3 subcells, ns =
+ * floor(L / side) (the paper: side 3 sigma), a subcell is gas when count / volume <
+ * gas_density (the paper: 0.2), and face-neighbouring gas subcells of the periodic
+ * simple cubic lattice form one bubble (site percolation). Outputs (may be NULL):
+ * ns_out; counts[ns^3] as unsigned char (saturated at 255, the paper's storage);
+ * n_bubbles; sizes[min(n_bubbles, cap)] = subcells per bubble, descending.
+ * Requires ns^3 < 2^31. Temporary device memory is allocated for the call. */
+MD_API int md_bubbles(md_ctx* ctx, double side, double gas_density, int32_t* ns_out, uint8_t* counts,
+                      int64_t* n_bubbles, int64_t* sizes, int64_t cap);
+
 /* Pair counts of the current list: entries (listed, r < rl at the build) and those
  * with r < rc at the current positions (FP64 test). */
 MD_API int md_pair_stats(md_ctx* ctx, int64_t* listed, int64_t* within_rc);

@@ -49,6 +49,8 @@ def _load():
             "orc_run_mode": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64,
                                        C.c_int, C.c_int]),
             "orc_pair_force_factor_rcp": (_D, [_D, _D, _D, C.c_int, C.c_int]),
+            "orc_subcell_counts": (None, [_I64, _D, C.c_int, _PD, _PI32]),
+            "orc_clusters": (_I64, [C.c_int, C.POINTER(C.c_uint8), _PI32]),
             "orc_forces_list_rcp": (None, [_I64, _D, _D, _D, _PD, _PI64, _PI32, C.c_int, C.c_int, _PD]),
         }
         for name, (res, args) in sig.items():
@@ -208,3 +210,33 @@ def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
     if rc_ != 0:
         raise MemoryError("oracle run failed to allocate")
     return dict(x=x, v=v, rebuilds=rebuilds.value, trace=trace)
+
+
+def subcell_counts(x, box: float, side: float = 3.0) -> tuple[np.ndarray, int]:
+    """Particles per subcell (Sec. 4.2), ns = floor(L / side) subcells per axis."""
+    x = _f64(x, (-1, 3))
+    ns = max(1, int(np.floor(box / side)))
+    counts = np.empty(ns ** 3, dtype=np.int32)
+    _load().orc_subcell_counts(x.shape[0], box, ns, _pd(x), counts.ctypes.data_as(_PI32))
+    return counts, ns
+
+
+def clusters(gas, ns: int) -> tuple[int, np.ndarray]:
+    """Face-connected clusters of gas subcells on the periodic ns^3 lattice:
+    (number of clusters, label per subcell = smallest index of its cluster or -1)."""
+    g = np.ascontiguousarray(np.asarray(gas, dtype=np.uint8).reshape(-1))
+    label = np.empty(ns ** 3, dtype=np.int32)
+    k = _load().orc_clusters(ns, g.ctypes.data_as(C.POINTER(C.c_uint8)), label.ctypes.data_as(_PI32))
+    return int(k), label
+
+
+def bubbles(x, box: float, side: float = 3.0, gas_density: float = 0.2) -> dict:
+    """Bubble identification of Sec. 4.2: subcell counts, gas where the density is
+    below gas_density, clusters by site percolation; sizes in subcells, descending."""
+    counts, ns = subcell_counts(x, box, side)
+    vol = (box / ns) ** 3
+    gas = counts.astype(np.float64) < gas_density * vol
+    k, label = clusters(gas, ns)
+    sizes = np.bincount(label[label >= 0]) if k else np.zeros(0, dtype=np.int64)
+    sizes = np.sort(sizes[sizes > 0])[::-1]
+    return dict(ns=ns, counts=counts, gas=gas, n_bubbles=k, sizes=sizes, label=label)

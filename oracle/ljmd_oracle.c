@@ -458,3 +458,57 @@ done:
     free(f);
     return rc_;
 }
+
+/* ------------------------------------------------ bubbles (Sec. 4.2) */
+
+/* Particles per subcell of the grid with ns subcells per axis (side L / ns):
+ * c_a = min(floor(x_a (ns / L)), ns - 1), index cx + ns (cy + ns cz); positions in [0, L). */
+ORC_API void orc_subcell_counts(int64_t n, double box, int ns, const double* x, int32_t* counts) {
+    double inv = (double)ns / box;
+    int64_t ncell = (int64_t)ns * ns * ns;
+    for (int64_t c = 0; c < ncell; ++c) counts[c] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            int k = (int)floor(x[3 * i + a] * inv);
+            if (k > ns - 1) k = ns - 1;
+            if (k < 0) k = 0;
+            c[a] = k;
+        }
+        counts[c[0] + ns * (c[1] + ns * c[2])] += 1;
+    }
+}
+
+/* Site percolation on the periodic simple cubic lattice (Sec. 4.2): subcells with
+ * gas[c] != 0 that share a face belong to the same cluster. Flood fill (breadth
+ * first) from every unlabelled gas cell in index order; label[c] = smallest index
+ * of c's cluster, -1 for non-gas cells. Returns the number of clusters. */
+ORC_API int64_t orc_clusters(int ns, const uint8_t* gas, int32_t* label) {
+    int64_t ncell = (int64_t)ns * ns * ns;
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ncell > 0 ? ncell : 1));
+    int64_t nclusters = 0;
+    for (int64_t c = 0; c < ncell; ++c) label[c] = -1;
+    for (int64_t c0 = 0; c0 < ncell; ++c0) {
+        if (!gas[c0] || label[c0] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = (int32_t)c0;
+        label[c0] = (int32_t)c0;
+        while (head < tail) {
+            int32_t c = queue[head++];
+            int cx = c % ns, cy = (c / ns) % ns, cz = c / (ns * ns);
+            int nb[6][3] = {{cx + 1, cy, cz}, {cx - 1, cy, cz}, {cx, cy + 1, cz},
+                            {cx, cy - 1, cz}, {cx, cy, cz + 1}, {cx, cy, cz - 1}};
+            for (int q = 0; q < 6; ++q) {
+                int x = (nb[q][0] + ns) % ns, y = (nb[q][1] + ns) % ns, z = (nb[q][2] + ns) % ns;
+                int32_t d = x + ns * (y + ns * z);
+                if (gas[d] && label[d] < 0) {
+                    label[d] = (int32_t)c0;
+                    queue[tail++] = d;
+                }
+            }
+        }
+        nclusters += 1;
+    }
+    free(queue);
+    return nclusters;
+}

@@ -242,6 +242,23 @@ int md_get_list(md_ctx* c, int64_t* start, int32_t* partners) {
   return c->eng.get_list(0, start, partners, c->stream);
 }
 
+int md_bubbles(md_ctx* c, double side, double gas_density, int32_t* ns_out, uint8_t* counts,
+               int64_t* n_bubbles, int64_t* sizes, int64_t cap) {
+  int r = check_ctx(c);
+  if (r) return r;
+  int ns = 0;
+  std::vector<uint32_t> cnt;
+  std::vector<int64_t> sz;
+  if ((r = c->eng.bubbles(0, side, gas_density, &ns, &cnt, &sz, c->stream))) return r;
+  if (ns_out) *ns_out = ns;
+  if (counts)
+    for (size_t q = 0; q < cnt.size(); ++q) counts[q] = (uint8_t)(cnt[q] > 255u ? 255u : cnt[q]);
+  if (n_bubbles) *n_bubbles = (int64_t)sz.size();
+  if (sizes)
+    for (int64_t q = 0; q < (int64_t)sz.size() && q < cap; ++q) sizes[q] = sz[(size_t)q];
+  return MD_OK;
+}
+
 int md_set_timing(md_ctx* c, int on) {
   int r = check_ctx(c);
   if (r) return r;

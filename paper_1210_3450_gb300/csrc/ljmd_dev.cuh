@@ -139,4 +139,9 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
 void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v,
                         int sys, int64_t ntiles_sys, cudaStream_t s);
 
+// Bubble identification of system `sys` (Sec. 4.2): subcell counts, gas where
+// count < gas_count, union-find labels (root = smallest index), cluster sizes.
+void launch_bubbles(const DevArrays& a, int cur, int sys, int64_t n, int ns, double box, double gas_count,
+                    uint32_t* counts, int32_t* parent, uint32_t* size, int* err, cudaStream_t s);
+
 }  // namespace ljmd

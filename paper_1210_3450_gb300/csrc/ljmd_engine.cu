@@ -797,6 +797,51 @@ int Engine::scale_velocities(const std::vector<double>& factor, cudaStream_t s) 
   return kOK;
 }
 
+int Engine::bubbles(int k, double side, double gas_density, int* ns_out, std::vector<uint32_t>* counts,
+                    std::vector<int64_t>* sizes, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  const SysHost& h = sys_[k];
+  if (!h.has_state) { set_error("no state set"); return kErrState; }
+  if (!(side > 0.0) || !std::isfinite(gas_density)) { set_error("need side > 0"); return kErrArg; }
+  const int64_t ns = std::max<int64_t>(1, (int64_t)std::floor(h.spec.L / side));
+  const int64_t ncell = ns * ns * ns;
+  if (ncell >= ((int64_t)1 << 31) - 1) { set_error("too many subcells (ns^3 >= 2^31)"); return kErrArg; }
+  uint32_t* d_counts = nullptr;
+  uint32_t* d_size = nullptr;
+  int32_t* d_parent = nullptr;
+  int* d_err = nullptr;
+  int r = dmalloc(&d_counts, ncell);
+  if (r == kOK) r = dmalloc(&d_size, ncell);
+  if (r == kOK) r = dmalloc(&d_parent, ncell);
+  if (r == kOK) r = dmalloc(&d_err, 1);
+  if (r != kOK) {
+    dfree(d_counts); dfree(d_size); dfree(d_parent); dfree(d_err);
+    return r;
+  }
+  const double vol = std::pow(h.spec.L / (double)ns, 3);
+  launch_bubbles(arrays(), cur_, k, h.spec.n, (int)ns, h.spec.L, gas_density * vol, d_counts, d_parent, d_size,
+                 d_err, s);
+  cudaError_t e = cudaGetLastError();
+  std::vector<int32_t> parent((size_t)ncell);
+  std::vector<uint32_t> size((size_t)ncell);
+  int herr = 0;
+  counts->assign((size_t)ncell, 0u);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts->data(), d_counts, sizeof(uint32_t) * ncell, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(parent.data(), d_parent, sizeof(int32_t) * ncell, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(size.data(), d_size, sizeof(uint32_t) * ncell, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(d_counts); dfree(d_size); dfree(d_parent); dfree(d_err);
+  if (e != cudaSuccess) { set_error(std::string("bubbles: ") + cudaGetErrorString(e)); return kErrCuda; }
+  if (herr) { set_error("bubbles: union-find retry bound reached"); return kErrTimeout; }
+  sizes->clear();
+  for (int64_t c = 0; c < ncell; ++c)
+    if (parent[(size_t)c] == (int32_t)c) sizes->push_back((int64_t)size[(size_t)c]);
+  std::sort(sizes->begin(), sizes->end(), [](int64_t a, int64_t b) { return a > b; });
+  *ns_out = (int)ns;
+  return kOK;
+}
+
 int Engine::build_lists(cudaStream_t s) {
   std::vector<int> which;
   for (int k = 0; k < nsys(); ++k) {

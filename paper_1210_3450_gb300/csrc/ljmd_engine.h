@@ -130,6 +130,11 @@ class Engine {
   int set_timing(bool on);
   void get_timing(double* out8) const;
   int pair_stats(int k, int64_t* listed, int64_t* inside, cudaStream_t s);
+  // Bubble identification (Sec. 4.2) of system k at its current positions:
+  // ns subcells per axis (side >= `side`), counts per subcell, bubble sizes
+  // (subcells) in descending order.
+  int bubbles(int k, double side, double gas_density, int* ns, std::vector<uint32_t>* counts,
+              std::vector<int64_t>* sizes, cudaStream_t s);
   // Device scratch of at least 6 * n doubles for caller-order staging.
   int stage(int64_t n, double** out);
 

@@ -72,6 +72,7 @@ SIGNATURES = {
     "md_list_size": (C.c_int, [_P, _PI64]),
     "md_get_list": (C.c_int, [_P, _PI64, _PI32]),
     "md_pair_stats": (C.c_int, [_P, _PI64, _PI64]),
+    "md_bubbles": (C.c_int, [_P, C.c_double, C.c_double, _PI32, C.POINTER(C.c_uint8), _PI64, _PI64, C.c_int64]),
     "md_set_timing": (C.c_int, [_P, C.c_int]),
     "md_get_timing": (C.c_int, [_P, _PD]),
     "md_forces_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, _P, _P]),
@@ -267,6 +268,20 @@ class LJSystem:
 
     def set_timing(self, on: bool = True):
         _check(_lib.md_set_timing(self._h, 1 if on else 0))
+
+    def bubbles(self, side: float = 3.0, gas_density: float = 0.2) -> dict:
+        """Bubble identification of Sec. 4.2 (md_bubbles): ns, uint8 subcell counts,
+        number of bubbles and their sizes in subcells (descending)."""
+        ns = max(1, int(np.floor(self.box / side)))
+        counts = np.empty(ns ** 3, dtype=np.uint8)
+        nb = C.c_int64()
+        nsr = C.c_int32()
+        cap = ns ** 3
+        sizes = np.empty(cap, dtype=np.int64)
+        _check(_lib.md_bubbles(self._h, float(side), float(gas_density), C.byref(nsr),
+                               counts.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(nb),
+                               sizes.ctypes.data_as(_PI64), cap))
+        return dict(ns=nsr.value, counts=counts, n_bubbles=nb.value, sizes=sizes[:nb.value].copy())
 
     def set_tuning(self, **kw):
         for k, v in kw.items():

@@ -12,7 +12,8 @@
   velocity rescaling every 10 steps, then expanded uniformly by 1.05 per axis
   (x -> 1.05 x, L -> 1.05 L, momenta kept; Sec. 4.1 of the paper uses 1.025) and
   run NVE with rc = 3.0 (the two-phase region: bubbles nucleate); reports
-  particle-steps/s, list rebuilds and the pressure after expansion.
+  particle-steps/s, list rebuilds, and every 1000 steps the pressure and the
+  bubbles found as in Sec. 4.2 (subcells of side 3, gas below density 0.2).
 * serve / serve-scaled: Poisson arrivals of LJ runs (N log-uniform in
   [1e3, 1e6], rho in [0.6, 0.85], T in [0.722, 1.2], steps in [1e3, 1e4])
   through the continuous-batching server; serve-scaled sets the arrival rate to
@@ -114,8 +115,11 @@ def cavitation(cells=160, equil_steps=2000, rescale_every=10, steps=20000, alpha
         sec += _cuda_time(lambda: s.step_async(k, cfg.dt, stream), stream)
         done += k
         o = s.observables()
+        b = s.bubbles(3.0, 0.2)
         series.append(dict(step=done, pressure=o["pressure"], temperature=o["temperature"],
-                           pe_per_particle=o["pe"] / n))
+                           pe_per_particle=o["pe"] / n, bubbles=b["n_bubbles"],
+                           largest_bubble_subcells=int(b["sizes"][0]) if b["n_bubbles"] else 0,
+                           gas_subcells=int(b["sizes"].sum())))
     tm = s.get_timing()
     rebuilds = s.stats()["rebuilds"] - r0
     s.close()

@@ -397,3 +397,82 @@ def test_reciprocal_approximation_eight_bits_below_1_256(oracle):
             fval = 24 * y ** 4 - 48 * y ** 7 - g
             y -= fval / (96 * y ** 3 - 336 * y ** 6)
         assert abs(y - y_exact) / y_exact < 1.0 / 256.0
+
+
+# ---------------------------------------------------- bubbles (Sec. 4.2)
+
+def _mask(ns, cells):
+    g = np.zeros(ns ** 3, dtype=np.uint8)
+    for (x, y, z) in cells:
+        g[x + ns * (y + ns * z)] = 1
+    return g
+
+
+@pytest.mark.parametrize("ns,cells,expect", [
+    (5, [], 0),
+    (5, [(2, 2, 2)], 1),
+    (5, [(0, 0, 0), (2, 2, 2)], 2),
+    (5, [(0, 0, 0), (4, 0, 0)], 1),                       # joined through the periodic face
+    (5, [(0, 0, 0), (1, 1, 0)], 2),                       # edge neighbours only: not joined
+    (5, [(1, 1, 1), (1, 1, 2), (1, 1, 3), (3, 3, 3)], 2),
+    (4, [(x, y, 0) for x in range(4) for y in range(4)], 1),   # a slab
+    (4, [(x, y, z) for x in range(4) for y in range(4) for z in range(4) if (x + y + z) % 2 == 0], 32),
+])
+def test_cluster_counts_hand_counted(oracle, ns, cells, expect):
+    """Site percolation on the periodic simple cubic lattice, hand-counted cases:
+    face neighbours join (also across the periodic faces), edge / corner
+    neighbours do not; a checkerboard has no face contacts."""
+    k, label = oracle.clusters(_mask(ns, cells), ns)
+    assert k == expect
+    for c in cells:
+        i = c[0] + ns * (c[1] + ns * c[2])
+        assert label[i] >= 0 and label[label[i]] == label[i]
+
+
+def test_cluster_labels_match_networkx_components(oracle):
+    """Random gas masks: clusters equal networkx connected components of the
+    periodic face-adjacency graph."""
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(7)
+    for ns, p in [(6, 0.2), (7, 0.3), (8, 0.35), (9, 0.5)]:
+        g = (rng.random(ns ** 3) < p).astype(np.uint8)
+        G = nx.Graph()
+        for c in np.flatnonzero(g):
+            G.add_node(int(c))
+            x, y, z = c % ns, (c // ns) % ns, c // (ns * ns)
+            for d in [((x + 1) % ns, y, z), (x, (y + 1) % ns, z), (x, y, (z + 1) % ns)]:
+                j = d[0] + ns * (d[1] + ns * d[2])
+                if g[j]:
+                    G.add_edge(int(c), int(j))
+        comps = list(nx.connected_components(G))
+        k, label = oracle.clusters(g, ns)
+        assert k == len(comps)
+        for comp in comps:
+            assert {int(label[c]) for c in comp} == {min(comp)}
+
+
+def test_subcell_counts_sum_and_bracket(oracle):
+    x, box = li.perturbed_fcc(4 * 8 ** 3, 0.7, 0.1, 13)
+    counts, ns = oracle.subcell_counts(x, box, 3.0)
+    assert ns == int(np.floor(box / 3.0)) and counts.sum() == len(x)
+    side = box / ns
+    c = np.minimum(np.floor(x / side).astype(int), ns - 1)
+    np.testing.assert_array_equal(np.bincount(c[:, 0] + ns * (c[:, 1] + ns * c[:, 2]), minlength=ns ** 3),
+                                  counts)
+
+
+def test_bubbles_of_carved_spheres(oracle):
+    """Particles removed from three well separated spheres of radius 4 (in a
+    dense lattice) give three gas clusters."""
+    n = 4 * 16 ** 3
+    box = li.box_length(n, 0.7)
+    x = li.fcc_positions(n, box)
+    centers = np.array([[0.2, 0.2, 0.2], [0.6, 0.25, 0.7], [0.3, 0.75, 0.55]]) * box
+    keep = np.ones(len(x), dtype=bool)
+    for cen in centers:
+        d = x - cen
+        d -= box * np.round(d / box)
+        keep &= (d * d).sum(1) > 4.0 ** 2
+    b = oracle.bubbles(x[keep], box)
+    assert b["n_bubbles"] == 3
+    assert b["sizes"].min() >= 1
