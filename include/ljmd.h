@@ -105,6 +105,14 @@ MD_API int md_step(md_ctx* ctx, int64_t nsteps, double dt);
  * validity decision, which is read back from the device every step). */
 MD_API int md_step_async(md_ctx* ctx, int64_t nsteps, double dt, void* stream);
 
+/* Nose-Hoover NVT steps (the thermostat of Sec. 4.1): each step is a thermostat half
+ * step, one velocity-Verlet step (md_step) and a thermostat half step, the reversible
+ * splitting: zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G'
+ * with G = (2 KE - 3 (N - 1) T) / Q. zeta and eta (thermostat velocity and position)
+ * are read and updated; KE + PE + Q zeta^2 / 2 + 3 (N - 1) T eta is conserved. */
+MD_API int md_step_nvt(md_ctx* ctx, int64_t nsteps, double dt, double T, double Q, double* zeta,
+                       double* eta);
+
 /* Forces at the current positions (N*3 host array): F_i = sum_j g(r)(x_j - x_i),
  * g = 24 r^-8 - 48 r^-14 + 8 c2 for r < rc (Algorithm 1's bracket, Sec. 3.3). */
 MD_API int md_forces(md_ctx* ctx, double* f);
@@ -273,6 +281,11 @@ MD_API int md_batch_get_state_dev(md_batch* b, int id, double* x_dev, double* v_
  * ignored). Blocks until done. */
 MD_API int md_batch_step(md_batch* b, int64_t nsteps, const double* dt);
 MD_API int md_batch_step_async(md_batch* b, int64_t nsteps, const double* dt, void* stream);
+
+/* Nose-Hoover NVT steps for every active system (arrays of max_systems doubles;
+ * zeta, eta read and updated), as md_step_nvt. */
+MD_API int md_batch_step_nvt(md_batch* b, int64_t nsteps, const double* dt, const double* T,
+                             const double* Q, double* zeta, double* eta);
 
 /* Forces of one system at its current positions (N*3 host array). */
 MD_API int md_batch_forces(md_batch* b, int id, double* f);

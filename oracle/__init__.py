@@ -50,6 +50,7 @@ def _load():
                                        C.c_int, C.c_int]),
             "orc_pair_force_factor_rcp": (_D, [_D, _D, _D, C.c_int, C.c_int]),
             "orc_subcell_counts": (None, [_I64, _D, C.c_int, _PD, _PI32]),
+            "orc_run_nvt": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _D, _D, _PD, _PI64, _PD, _I64]),
             "orc_clusters": (_I64, [C.c_int, C.POINTER(C.c_uint8), _PI32]),
             "orc_forces_list_rcp": (None, [_I64, _D, _D, _D, _PD, _PI64, _PI32, C.c_int, C.c_int, _PD]),
         }
@@ -240,3 +241,24 @@ def bubbles(x, box: float, side: float = 3.0, gas_density: float = 0.2) -> dict:
     sizes = np.bincount(label[label >= 0]) if k else np.zeros(0, dtype=np.int64)
     sizes = np.sort(sizes[sizes > 0])[::-1]
     return dict(ns=ns, counts=counts, gas=gas, n_bubbles=k, sizes=sizes, label=label)
+
+
+def run_nvt(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float, temperature: float,
+            q: float, zeta: float = 0.0, eta: float = 0.0, trace_every: int = 0) -> dict:
+    """Nose-Hoover NVT run (Sec. 4.1 thermostat; reversible splitting: thermostat half
+    step, velocity-Verlet step, thermostat half step). Returns dict(x, v, zeta, eta,
+    trace) where trace is KE + PE + Q zeta^2/2 + g T eta (the conserved quantity)."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    ze = np.array([zeta, eta], dtype=np.float64)
+    rebuilds = _I64(0)
+    trace = None
+    tp = None
+    if trace_every > 0:
+        trace = np.empty(1 + nsteps // trace_every)
+        tp = _pd(trace)
+    r = _load().orc_run_nvt(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt, temperature, q,
+                            _pd(ze), C.byref(rebuilds), tp, trace_every)
+    if r != 0:
+        raise MemoryError("oracle run failed")
+    return dict(x=x, v=v, zeta=float(ze[0]), eta=float(ze[1]), trace=trace, rebuilds=rebuilds.value)

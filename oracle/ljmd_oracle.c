@@ -512,3 +512,71 @@ ORC_API int64_t orc_clusters(int ns, const uint8_t* gas, int32_t* label) {
     free(queue);
     return nclusters;
 }
+
+/* ------------------------------------------- Nose-Hoover NVT (Sec. 4.1) */
+
+/* Thermostat half step of the reversible (RESPA / Trotter) splitting of the
+ * Nose-Hoover equations (thermostat variable zeta with mass Q, position eta):
+ *   zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G',
+ * with G = (2 KE - g T) / Q, g = 3 (N - 1) degrees of freedom. */
+static void nh_half(int64_t n, double* v, double dt, double temp, double q, double* zeta, double* eta) {
+    double ke = 0.0;
+    for (int64_t k = 0; k < 3 * n; ++k) ke += v[k] * v[k];
+    ke *= 0.5;
+    double g = 3.0 * (double)(n - 1);
+    *zeta += 0.25 * dt * (2.0 * ke - g * temp) / q;
+    *eta += 0.5 * dt * (*zeta);
+    double sc = exp(-0.5 * dt * (*zeta));
+    for (int64_t k = 0; k < 3 * n; ++k) v[k] = v[k] * sc;
+    ke = ke * sc * sc;
+    *zeta += 0.25 * dt * (2.0 * ke - g * temp) / q;
+}
+
+/* NVT run: each step is a thermostat half step, one velocity-Verlet step (with the
+ * list check and rebuild of orc_run) and a thermostat half step. zeta_eta[2] is
+ * read and updated. trace (optional) gets the conserved quantity
+ * KE + PE + Q zeta^2 / 2 + g T eta at step 0 and every trace_every steps. */
+ORC_API int orc_run_nvt(int64_t n, double box, double rc, double skin, double* x, double* v,
+                        int64_t nsteps, double dt, double temp, double q, double* zeta_eta,
+                        int64_t* rebuilds, double* trace, int64_t trace_every) {
+    double zeta = zeta_eta[0], eta = zeta_eta[1];
+    double g = 3.0 * (double)(n - 1);
+    int64_t ti = 0, rb_total = 0;
+    if (trace) {
+        double c2, c0, o[5];
+        orc_lj_coeffs(rc, &c2, &c0);
+        int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+        int64_t cap = n * 128 + 64;
+        int32_t* partners = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+        orc_wrap(n, box, x);
+        orc_build_list(n, box, rc + skin, x, start, partners, cap);
+        orc_observables_list(n, box, rc, c2, c0, x, v, start, partners, o);
+        trace[ti++] = o[0] + o[2] + 0.5 * q * zeta * zeta + g * temp * eta;
+        free(start);
+        free(partners);
+    }
+    for (int64_t step = 1; step <= nsteps; ++step) {
+        nh_half(n, v, dt, temp, q, &zeta, &eta);
+        int64_t rb = 0;
+        int r = orc_run(n, box, rc, skin, x, v, 1, dt, &rb, NULL, 0);
+        if (r) return r;
+        rb_total += rb;
+        nh_half(n, v, dt, temp, q, &zeta, &eta);
+        if (trace && trace_every > 0 && step % trace_every == 0) {
+            double c2, c0, o[5];
+            orc_lj_coeffs(rc, &c2, &c0);
+            int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+            int64_t cap = n * 128 + 64;
+            int32_t* partners = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+            orc_build_list(n, box, rc + skin, x, start, partners, cap);
+            orc_observables_list(n, box, rc, c2, c0, x, v, start, partners, o);
+            trace[ti++] = o[0] + o[2] + 0.5 * q * zeta * zeta + g * temp * eta;
+            free(start);
+            free(partners);
+        }
+    }
+    zeta_eta[0] = zeta;
+    zeta_eta[1] = eta;
+    if (rebuilds) *rebuilds = rb_total;
+    return 0;
+}

@@ -1,5 +1,6 @@
 // C ABI of the LJ-MD library (declared in include/ljmd.h): argument checks and
 // host <-> device marshalling around the engine. Each md_ctx is one system.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -140,6 +141,20 @@ int md_step(md_ctx* c, int64_t nsteps, double dt) {
   if (r) return r;
   std::vector<double> dts{dt};
   return c->eng.step(nsteps, dts, c->stream);
+}
+
+int md_step_nvt(md_ctx* c, int64_t nsteps, double dt, double T, double Q, double* zeta, double* eta) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!zeta || !eta) {
+    set_error("null thermostat state");
+    return MD_ERR_ARG;
+  }
+  std::vector<double> d{dt}, t{T}, q{Q}, z{*zeta}, e{*eta};
+  r = c->eng.step_nvt(nsteps, d, t, q, z, e, c->stream);
+  *zeta = z[0];
+  *eta = e[0];
+  return r;
 }
 
 int md_forces(md_ctx* c, double* f) {
@@ -532,6 +547,22 @@ int md_batch_step(md_batch* b, int64_t nsteps, const double* dt) {
   int r = check_batch(b);
   if (r) return r;
   return md_batch_step_async(b, nsteps, dt, b->stream);
+}
+
+int md_batch_step_nvt(md_batch* b, int64_t nsteps, const double* dt, const double* T, const double* Q,
+                      double* zeta, double* eta) {
+  int r = check_batch(b);
+  if (r) return r;
+  if (!dt || !T || !Q || !zeta || !eta) {
+    set_error("null argument");
+    return MD_ERR_ARG;
+  }
+  const int ns = b->eng.nsys();
+  std::vector<double> d(dt, dt + ns), t(T, T + ns), q(Q, Q + ns), z(zeta, zeta + ns), e(eta, eta + ns);
+  r = b->eng.step_nvt(nsteps, d, t, q, z, e, b->stream);
+  std::copy(z.begin(), z.end(), zeta);
+  std::copy(e.begin(), e.end(), eta);
+  return r;
 }
 
 int md_batch_forces(md_batch* b, int id, double* f) {

@@ -37,6 +37,7 @@ struct SysParams {
   double rl2;        // (rc + skin)^2
   double c2, c0;     // Eq. 1 coefficients
   double dt;         // time step of the current md_step call
+  double hdt;        // dt / 2 (a half kick)
   double qscale;     // 2^32 / L: fixed-point scale of the shadow positions
   float qunit;       // L / 2^32 as float: fixed-point unit
   float rl2q_lo;     // rl^2 (1 - 1e-5) in fixed-point units^2: certainly inside below
@@ -70,6 +71,8 @@ enum StepFlags : int {
   kStepDrift = 1,       // drift x by dt v after the kicks (writes the other x buffer)
   kStepStoreF = 2,      // store F (double) for md_forces / the next call
   kStepUseStoredF = 4,  // take F from the stored buffer instead of the pair loop
+  kStepKickA = 8,       // v += dt/2 F completing the previous step
+  kStepKickB = 16,      // v += dt/2 F, first half-kick of the next step
 };
 
 struct DevArrays {

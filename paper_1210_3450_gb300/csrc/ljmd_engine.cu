@@ -491,6 +491,7 @@ int Engine::upload_params(int only) {
     P.c2 = h.c2;
     P.c0 = h.c0;
     P.dt = h.dt;
+    P.hdt = 0.5 * h.dt;
     P.qscale = 4294967296.0 / h.spec.L;
     P.qunit = (float)(h.spec.L / 4294967296.0);
     P.rl2q_lo = (float)(P.rl2 * P.qscale * P.qscale * (1.0 - 1e-5));
@@ -665,6 +666,10 @@ int Engine::ensure_lists(cudaStream_t s) {
 
 int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
   const DevArrays a = arrays();
+  // the kicks are half steps: ka, kb in {0, 1/2} become flags (the kernels take
+  // dt/2 from the system parameters, so they need no FP64 compare or product)
+  if (ka != 0.0) flags |= kStepKickA;
+  if (kb != 0.0) flags |= kStepKickB;
   tmark_begin(kTStep, s);
   if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
   else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, precision_ >= 2 ? precision_ - 1 : 0, s);
@@ -783,6 +788,50 @@ int Engine::observables(double* out3, cudaStream_t s, bool with_pairs, const int
   CK(cudaMemcpyAsync(h_obs_, d_obs_, sizeof(double) * 3 * nsys(), cudaMemcpyDeviceToHost, s));
   CKR(sync_check(s));
   std::memcpy(out3, h_obs_, sizeof(double) * 3 * nsys());
+  return kOK;
+}
+
+int Engine::step_nvt(int64_t nsteps, const std::vector<double>& dt, const std::vector<double>& T,
+                     const std::vector<double>& Q, std::vector<double>& zeta, std::vector<double>& eta,
+                     cudaStream_t s) {
+  const int ns = nsys();
+  if (nsteps < 0 || (int)dt.size() != ns || (int)T.size() != ns || (int)Q.size() != ns ||
+      (int)zeta.size() != ns || (int)eta.size() != ns) {
+    set_error("step_nvt: one dt, T, Q, zeta, eta per system");
+    return kErrArg;
+  }
+  for (int k = 0; k < ns; ++k) {
+    if (!sys_[k].active) continue;
+    if (!(Q[k] > 0.0) || !(T[k] >= 0.0) || !std::isfinite(dt[k])) {
+      set_error("step_nvt: need Q > 0, T >= 0, finite dt");
+      return kErrArg;
+    }
+  }
+  std::vector<double> o3((size_t)(3 * ns)), fac((size_t)ns, 1.0);
+  // zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G',
+  // G = (2 KE - g T) / Q with g = 3 (N - 1)
+  auto half = [&]() -> int {
+    CKR(observables(o3.data(), s, false));
+    for (int k = 0; k < ns; ++k) {
+      fac[(size_t)k] = 1.0;
+      if (!sys_[k].active) continue;
+      const double g = 3.0 * (double)(sys_[k].spec.n - 1);
+      double ke = o3[(size_t)(3 * k + 2)];
+      zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
+      eta[k] += 0.5 * dt[k] * zeta[k];
+      const double sc = std::exp(-0.5 * dt[k] * zeta[k]);
+      fac[(size_t)k] = sc;
+      ke = ke * sc * sc;
+      zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
+    }
+    return scale_velocities(fac, s);
+  };
+  CKR(ensure_lists(s));
+  for (int64_t it = 0; it < nsteps; ++it) {
+    CKR(half());
+    CKR(step(1, dt, s));
+    CKR(half());
+  }
   return kOK;
 }
 

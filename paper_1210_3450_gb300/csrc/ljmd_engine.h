@@ -108,6 +108,12 @@ class Engine {
   // Advance every active system by nsteps steps of its own dt (dt per system id;
   // entries of inactive ids are ignored).
   int step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s);
+  // Nose-Hoover NVT (Sec. 4.1): per step a thermostat half step, one
+  // velocity-Verlet step, a thermostat half step (reversible splitting); T, Q,
+  // zeta, eta per system id (zeta, eta read and updated).
+  int step_nvt(int64_t nsteps, const std::vector<double>& dt, const std::vector<double>& T,
+               const std::vector<double>& Q, std::vector<double>& zeta, std::vector<double>& eta,
+               cudaStream_t s);
   // Observables (pe, virial, ke) of every active system into host out3[3 * nsys].
   // select: nsys flags choosing the systems (NULL = every active system); the
   // entries of unselected systems in out3 are unspecified.

@@ -468,9 +468,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
 namespace {
 
 // Velocity-Verlet update of one particle after its force F is known:
-//   v += ka dt F (completes the previous step), v += kb dt F (first half-kick of
-//   the next step; kept as two roundings so that a run split over several calls
-//   equals one uninterrupted call bit for bit), then optionally the drift
+//   v += dt/2 F (flag kStepKickA: completes the previous step), v += dt/2 F (flag
+//   kStepKickB: first half-kick of the next step; kept as two roundings so that a
+//   run split over several calls equals one uninterrupted call bit for bit), then
+//   optionally the drift
 //   x' = x + dt v into x[cur ^ 1] (not wrapped: list images stay valid) and the
 //   squared displacement since the list build for the validity check.
 template <bool kFP32>
@@ -480,8 +481,9 @@ __device__ __forceinline__ unsigned long long integrate(const DevArrays& a, cons
   if (flags & kStepStoreF) a.f[t.s] = make_double4_32a(Fx, Fy, Fz, 0.0);
   double4_32a v = a.v[t.s];
   const double dt = P.dt;
-  if (ka != 0.0) { const double h = ka * dt; v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
-  if (kb != 0.0) { const double h = kb * dt; v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
+  const double h = P.hdt;
+  if (flags & kStepKickA) { v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
+  if (flags & kStepKickB) { v.x = fma(h, Fx, v.x); v.y = fma(h, Fy, v.y); v.z = fma(h, Fz, v.z); }
   a.v[t.s] = v;
   if (!(flags & kStepDrift)) return 0ull;
   double4_32a xn;

@@ -60,6 +60,8 @@ SIGNATURES = {
     "md_step": (C.c_int, [_P, C.c_int64, C.c_double]),
     "md_step_async": (C.c_int, [_P, C.c_int64, C.c_double, _P]),
     "md_forces": (C.c_int, [_P, _PD]),
+    "md_step_nvt": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, C.c_double, _PD, _PD]),
+    "md_batch_step_nvt": (C.c_int, [_P, C.c_int64, _PD, _PD, _PD, _PD, _PD]),
     "md_forces_dev": (C.c_int, [_P, _P, _P]),
     "md_observables": (C.c_int, [_P, _PD, _PD, _PD, _PD, _PD]),
     "md_stats": (C.c_int, [_P, _PI64, _PI64]),
@@ -224,6 +226,14 @@ class LJSystem:
         f = np.empty((self.n, 3))
         _check(_lib.md_forces(self._h, _pd(f)))
         return f
+
+    def step_nvt(self, nsteps: int, dt: float, temperature: float, q: float, zeta: float = 0.0,
+                 eta: float = 0.0) -> tuple[float, float]:
+        """Nose-Hoover NVT steps (md_step_nvt); returns the updated (zeta, eta)."""
+        z, e = C.c_double(zeta), C.c_double(eta)
+        _check(_lib.md_step_nvt(self._h, int(nsteps), float(dt), float(temperature), float(q),
+                                C.byref(z), C.byref(e)))
+        return z.value, e.value
 
     def forces_dev(self, f, stream=None):
         _check(_lib.md_forces_dev(self._h, _dev_ptr(f, self.n), _stream_ptr(stream)))

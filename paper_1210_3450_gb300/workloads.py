@@ -8,8 +8,9 @@
 * batched: independent replica systems (N log-uniform in [500, 32000], rho in
   [0.60, 0.85], T in [0.7, 1.2], rc 2.5, dt 0.005) stepped together, one launch
   per kernel per step for the whole batch.
-* cavitation: a 16,384,000-particle liquid at rho 0.70 held at T = 0.90 by
-  velocity rescaling every 10 steps, then expanded uniformly by 1.05 per axis
+* cavitation: a 16,384,000-particle liquid at rho 0.70 held at T = 0.90 by a
+  Nose-Hoover thermostat (Sec. 4.1; or velocity rescaling every 10 steps with
+  --thermostat rescale), then expanded uniformly by 1.05 per axis
   (x -> 1.05 x, L -> 1.05 L, momenta kept; Sec. 4.1 of the paper uses 1.025) and
   run NVE with rc = 3.0 (the two-phase region: bubbles nucleate); reports
   particle-steps/s, list rebuilds, and every 1000 steps the pressure and the
@@ -74,7 +75,7 @@ def batched(count=256, steps=2000, warmup=20, precision=1, seed=1004) -> dict:
 
 
 def cavitation(cells=160, equil_steps=2000, rescale_every=10, steps=20000, alpha=1.05, precision=1,
-               obs_every=1000) -> dict:
+               obs_every=1000, thermostat="nose-hoover", tau=0.5) -> dict:
     import numpy as np
     import torch
     import lj_inputs as li
@@ -84,10 +85,15 @@ def cavitation(cells=160, equil_steps=2000, rescale_every=10, steps=20000, alpha
     s = ljmd.LJSystem(cfg.box, n, cfg.rc, cfg.skin, precision)
     s.set_state(cfg.x, cfg.v)
     t_eq = time.perf_counter()
-    for _ in range(equil_steps // rescale_every):
-        s.step(rescale_every, cfg.dt)
-        t = 2.0 * s.kinetic_energy() / (3.0 * (n - 1))
-        s.scale_velocities(math.sqrt(cfg.temperature / t))
+    if thermostat == "nose-hoover":
+        # Nose-Hoover with thermostat period tau: Q = g T tau^2 / (4 pi^2) ~ g T tau^2 / 40
+        q = 3.0 * (n - 1) * cfg.temperature * tau * tau / (4.0 * math.pi ** 2)
+        zeta, eta = s.step_nvt(equil_steps, cfg.dt, cfg.temperature, q)
+    else:
+        for _ in range(equil_steps // rescale_every):
+            s.step(rescale_every, cfg.dt)
+            t = 2.0 * s.kinetic_energy() / (3.0 * (n - 1))
+            s.scale_velocities(math.sqrt(cfg.temperature / t))
     t_eq = time.perf_counter() - t_eq
     obs0 = s.observables()
     xd = torch.empty(n, 3, dtype=torch.float64, device="cuda")
@@ -129,7 +135,7 @@ def cavitation(cells=160, equil_steps=2000, rescale_every=10, steps=20000, alpha
                 steps_per_build=steps / max(rebuilds, 1),
                 kernel_ms_per_step=tm["step_ms"] / max(tm["step_launches"], 1),
                 list_build_ms_per_launch=tm["list_ms"] / max(tm["list_launches"], 1),
-                equilibration=dict(steps=equil_steps, rescale_every=rescale_every, seconds=t_eq,
+                equilibration=dict(steps=equil_steps, thermostat=thermostat, seconds=t_eq,
                                    pressure=obs0["pressure"], temperature=obs0["temperature"]),
                 series=series, precision="fp32-force" if precision == 1 else "fp64")
 
@@ -169,6 +175,7 @@ def main(argv=None):
     p.add_argument("--budget-gb", type=float, default=100.0)
     p.add_argument("--drain-limit", type=float, default=None)
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--thermostat", choices=["nose-hoover", "rescale"], default="nose-hoover")
     a = p.parse_args(argv)
     from . import build
     build.build()
@@ -176,7 +183,8 @@ def main(argv=None):
     if a.which == "batched":
         out = batched(a.count, a.steps or 2000, precision=prec)
     elif a.which == "cavitation":
-        out = cavitation(a.cells, a.equil_steps, steps=a.steps or 20000, precision=prec)
+        out = cavitation(a.cells, a.equil_steps, steps=a.steps or 20000, precision=prec,
+                         thermostat=a.thermostat)
     elif a.which == "serve":
         out = serve_run(a.rate, a.duration, a.budget_gb, drain_limit=a.drain_limit, precision=prec)
     else:

@@ -476,3 +476,56 @@ def test_bubbles_of_carved_spheres(oracle):
     b = oracle.bubbles(x[keep], box)
     assert b["n_bubbles"] == 3
     assert b["sizes"].min() >= 1
+
+
+# ------------------------------------------------- Nose-Hoover NVT (Sec. 4.1)
+
+def _nvt_start(n=256, rho=0.7, t0=1.4, seed=21):
+    x, box = li.perturbed_fcc(n, rho, 0.05, seed)
+    v = li.maxwell_boltzmann(n, t0, seed + 1)
+    return x, v, box
+
+
+def test_nvt_infinite_mass_is_nve(oracle):
+    """With Q -> infinity and zeta = 0 the thermostat never acts: NVT = NVE."""
+    x, v, box = _nvt_start()
+    a = oracle.run_nvt(x, v, box, 3.0, 0.3, 60, 0.005, 0.9, 1e300)
+    b = oracle.run(x, v, box, 3.0, 0.3, 60, 0.005)
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["v"], b["v"])
+
+
+def test_nvt_conserved_quantity_second_order(oracle):
+    """KE + PE + Q zeta^2 / 2 + g T eta is conserved up to O(dt^2)."""
+    x, v, box = _nvt_start()
+    errs = []
+    for dt, nst in [(0.004, 150), (0.002, 300)]:
+        r = oracle.run_nvt(x, v, box, 3.0, 0.3, nst, dt, 0.9, 20.0, trace_every=1)
+        errs.append(np.abs(r["trace"] - r["trace"][0]).max())
+    assert 2.8 < errs[0] / errs[1] < 5.5, errs
+    assert errs[0] / 256 < 2e-3
+
+
+def test_nvt_time_reversible(oracle):
+    x, v, box = _nvt_start()
+    f = oracle.run_nvt(x, v, box, 3.0, 0.3, 80, 0.003, 0.9, 10.0)
+    b = oracle.run_nvt(f["x"], -f["v"], box, 3.0, 0.3, 80, 0.003, 0.9, 10.0, zeta=-f["zeta"], eta=f["eta"])
+    d = b["x"] - oracle.wrap(x, box)
+    d -= box * np.round(d / box)
+    assert np.abs(d).max() < 1e-9
+    assert np.abs(b["v"] + v).max() < 1e-9
+    assert abs(b["zeta"]) < 1e-9
+
+
+def test_nvt_holds_the_temperature(oracle):
+    """Started hot (T = 1.4), the Nose-Hoover run settles at the target 0.9: the
+    mean over the last 1000 of 2000 steps is within 5 % (256 particles)."""
+    x, v, box = _nvt_start()
+    r = oracle.run_nvt(x, v, box, 3.0, 0.3, 1000, 0.005, 0.9, 5.0)
+    temps = []
+    xs, vs, z, e = r["x"], r["v"], r["zeta"], r["eta"]
+    for _ in range(10):
+        r = oracle.run_nvt(xs, vs, box, 3.0, 0.3, 100, 0.005, 0.9, 5.0, zeta=z, eta=e)
+        xs, vs, z, e = r["x"], r["v"], r["zeta"], r["eta"]
+        temps.append(float((vs ** 2).sum() / (3 * (len(xs) - 1))))
+    assert abs(np.mean(temps) - 0.9) < 0.05 * 0.9
