@@ -208,12 +208,15 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
  *   MD_TUNE_LIST_VARIANT pair-list build variant: bit 0 prunes neighbour rows and
  *                        narrows their x windows by the y / z distance to the row,
  *                        bit 1 writes list entries four at a time (0..3)
- * Defaults 128 / 2 / 128 / 0. The autotuner (paper_1210_3450_gb300.autotune) times the
+ *   MD_TUNE_STEP_HINT    1: L1 eviction hints on the FP32 step kernel's loads (list
+ *                        words not kept in L1, partner positions kept)
+ * Defaults 128 / 2 / 128 / 0 / 0. The autotuner (paper_1210_3450_gb300.autotune) times the
  * choices on the caller's own systems and sets the fastest. */
 #define MD_TUNE_STEP_BLOCK 0
 #define MD_TUNE_STEP_GROUPS 1
 #define MD_TUNE_LIST_BLOCK 2
 #define MD_TUNE_LIST_VARIANT 3
+#define MD_TUNE_STEP_HINT 4
 MD_API int md_set_tuning(md_ctx* ctx, int key, int value);
 MD_API int md_get_tuning(md_ctx* ctx, int key, int* value);
 

@@ -22,6 +22,7 @@ DEFAULT_CACHE = os.path.join(_HERE, "_build", "autotune.json")
 
 STEP_BLOCKS = (64, 128, 256)
 STEP_GROUPS = (1, 2)
+STEP_HINTS = (0, 1)
 LIST_BLOCKS = (64, 128, 256)
 LIST_VARIANTS = (0, 1, 2, 3)
 
@@ -56,18 +57,19 @@ def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None 
         if known:
             system.set_tuning(**known["tuning"])
             return known
-    step_choices = list(itertools.product(STEP_BLOCKS, STEP_GROUPS if fp32 else (1,)))
+    step_choices = list(itertools.product(STEP_BLOCKS, STEP_GROUPS if fp32 else (1,),
+                                          STEP_HINTS if fp32 else (0,)))
     results = {}
     system.step(5, dt)
-    for blk, grp in step_choices:
-        system.set_tuning(step_block=blk, step_groups=grp)
+    for blk, grp, hint in step_choices:
+        system.set_tuning(step_block=blk, step_groups=grp, step_hint=hint)
         system.step(2, dt)
         system.set_timing(True)
         system.step(steps, dt)
         t = system.get_timing()
-        results[f"step{blk}x{grp}"] = t["step_ms"] / max(t["step_launches"], 1)
-    blk, grp = min(step_choices, key=lambda c: results[f"step{c[0]}x{c[1]}"])
-    system.set_tuning(step_block=blk, step_groups=grp)
+        results[f"step{blk}x{grp}h{hint}"] = t["step_ms"] / max(t["step_launches"], 1)
+    blk, grp, hint = min(step_choices, key=lambda c: results[f"step{c[0]}x{c[1]}h{c[2]}"])
+    system.set_tuning(step_block=blk, step_groups=grp, step_hint=hint)
     list_times = {}
     for lb, lv in itertools.product(LIST_BLOCKS, LIST_VARIANTS):
         system.set_tuning(list_block=lb, list_variant=lv)
@@ -79,7 +81,8 @@ def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None 
             list_times[(lb, lv)] = t["list_ms"] / t["list_launches"]
     lbest, lvar = min(list_times, key=list_times.get) if list_times else (128, 0)
     system.set_tuning(list_block=lbest, list_variant=lvar)
-    out = dict(tuning=dict(step_block=blk, step_groups=grp, list_block=lbest, list_variant=lvar),
+    out = dict(tuning=dict(step_block=blk, step_groups=grp, step_hint=hint, list_block=lbest,
+                           list_variant=lvar),
                step_ms=results, list_ms={f"{k[0]}v{k[1]}": v for k, v in list_times.items()})
     if cache and key:
         data = _load(cache)

@@ -112,6 +112,7 @@ struct Tuning {
   int step_groups = 2;
   int list_block = 128;
   int list_variant = 0;  // bit 0: row pruning by y / z distance; bit 1: 16-byte list writes
+  int step_hint = 0;     // 1: L1 eviction hints on the FP32 step kernel's loads
 };
 
 // ---------------------------------------------------------------- launchers

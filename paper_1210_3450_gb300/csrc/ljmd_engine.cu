@@ -110,6 +110,10 @@ int Engine::set_tuning(int key, int value) {
       if (value < 0 || value > 3) break;
       tuning_.list_variant = value;
       return kOK;
+    case 4:
+      if (value != 0 && value != 1) break;
+      tuning_.step_hint = value;
+      return kOK;
     default:
       break;
   }
@@ -119,7 +123,7 @@ int Engine::set_tuning(int key, int value) {
 
 int Engine::get_tuning(int key) const {
   return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block
-         : key == 3 ? tuning_.list_variant : -1;
+         : key == 3 ? tuning_.list_variant : key == 4 ? tuning_.step_hint : -1;
 }
 
 int Engine::set_timing(bool on) {

@@ -545,13 +545,31 @@ __device__ __forceinline__ void pair_fp32(const int4& qi, const int4& qj, bool v
 
 }  // namespace
 
+// Loads with L1 eviction hints: list words are read once (no L1 allocation), the
+// partners' shadow positions are reused by neighbouring threads (kept in L1).
+__device__ __forceinline__ uint4 ld_list(const uint4* p, bool hint) {
+  if (!hint) return __ldg(p);
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ int4 ld_shadow(const int4* p, bool hint) {
+  if (!hint) return *p;
+  int4 r;
+  asm("ld.global.nc.L1::evict_last.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
 // FP32-force form: pair arithmetic in FP32 from fixed-point separations (the
 // wrapped integer difference is already the minimum image). Each iteration
 // takes GROUPS x 4 partners (GROUPS 16-byte list loads, then 4 GROUPS gathers in
 // flight at once) and the next iteration's list loads are issued before this
 // iteration's gathers are used (software pipelining, the role of Algorithm 1's
 // unrolling). BLOCK and GROUPS are chosen by the autotuner.
-template <int BLOCK, int GROUPS>
+template <int BLOCK, int GROUPS, bool HINT>
 __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, double ka, double kb, int flags) {
   TileCtx t;
   SysParams P;
@@ -577,12 +595,12 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
     const int ng = (cnt + 3) >> 2;
     uint4 e[GROUPS];
 #pragma unroll
-    for (int u = 0; u < GROUPS; ++u) e[u] = u < ng ? __ldg(lp4 + (int64_t)u * kTile) : none;
+    for (int u = 0; u < GROUPS; ++u) e[u] = u < ng ? ld_list(lp4 + (int64_t)u * kTile, HINT) : none;
     for (int g = 0; g < ng; g += GROUPS) {
       uint4 en[GROUPS];
 #pragma unroll
       for (int u = 0; u < GROUPS; ++u)
-        en[u] = (g + GROUPS + u < ng) ? __ldg(lp4 + (int64_t)(g + GROUPS + u) * kTile) : none;
+        en[u] = (g + GROUPS + u < ng) ? ld_list(lp4 + (int64_t)(g + GROUPS + u) * kTile, HINT) : none;
       int4 q[4 * GROUPS];
       bool ok[4 * GROUPS];
 #pragma unroll
@@ -592,10 +610,10 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
         ok[4 * u + 1] = rem > 1;
         ok[4 * u + 2] = rem > 2;
         ok[4 * u + 3] = rem > 3;
-        q[4 * u + 0] = qs[ok[4 * u + 0] ? (e[u].x & kIdxMask) : self];
-        q[4 * u + 1] = qs[ok[4 * u + 1] ? (e[u].y & kIdxMask) : self];
-        q[4 * u + 2] = qs[ok[4 * u + 2] ? (e[u].z & kIdxMask) : self];
-        q[4 * u + 3] = qs[ok[4 * u + 3] ? (e[u].w & kIdxMask) : self];
+        q[4 * u + 0] = ld_shadow(qs + (ok[4 * u + 0] ? (e[u].x & kIdxMask) : self), HINT);
+        q[4 * u + 1] = ld_shadow(qs + (ok[4 * u + 1] ? (e[u].y & kIdxMask) : self), HINT);
+        q[4 * u + 2] = ld_shadow(qs + (ok[4 * u + 2] ? (e[u].z & kIdxMask) : self), HINT);
+        q[4 * u + 3] = ld_shadow(qs + (ok[4 * u + 3] ? (e[u].w & kIdxMask) : self), HINT);
       }
 #pragma unroll
       for (int m = 0; m < 4 * GROUPS; ++m) pair_fp32(qi, q[m], ok[m], qu, rc2, c2x8, fx, fy, fz);
@@ -892,16 +910,17 @@ void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int fla
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s) {
   const int b = tu.step_block, g = tu.step_groups;
-#define LJMD_STEP32(B, G) k_step_fp32<B, G><<<blocks_of(a, B), B, 0, s>>>(a, cur, ka, kb, flags)
-  if (g == 2) {
-    if (b == 64) LJMD_STEP32(64, 2);
-    else if (b == 256) LJMD_STEP32(256, 2);
-    else LJMD_STEP32(128, 2);
+#define LJMD_STEP32(B, G, H) k_step_fp32<B, G, H><<<blocks_of(a, B), B, 0, s>>>(a, cur, ka, kb, flags)
+#define LJMD_STEP32B(G, H)             \
+  if (b == 64) LJMD_STEP32(64, G, H);  \
+  else if (b == 256) LJMD_STEP32(256, G, H); \
+  else LJMD_STEP32(128, G, H)
+  if (tu.step_hint) {
+    if (g == 2) { LJMD_STEP32B(2, true); } else { LJMD_STEP32B(1, true); }
   } else {
-    if (b == 64) LJMD_STEP32(64, 1);
-    else if (b == 256) LJMD_STEP32(256, 1);
-    else LJMD_STEP32(128, 1);
+    if (g == 2) { LJMD_STEP32B(2, false); } else { LJMD_STEP32B(1, false); }
   }
+#undef LJMD_STEP32B
 #undef LJMD_STEP32
 }
 void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, const int32_t* select, cudaStream_t s) {

@@ -32,6 +32,7 @@ def main(argv=None):
     p.add_argument("--step-block", type=int, default=None)
     p.add_argument("--step-groups", type=int, default=None)
     p.add_argument("--list-block", type=int, default=None)
+    p.add_argument("--step-hint", type=int, default=None)
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args(argv)
     import lj_inputs as li
@@ -45,7 +46,8 @@ def main(argv=None):
     mode = MD_FP32_FORCE if a.precision == "fp32" else MD_FP64
     with LJSystem(box, n, a.rc, a.skin, mode) as s:
         tun = {k: val for k, val in dict(step_block=a.step_block, step_groups=a.step_groups,
-                                         list_block=a.list_block).items() if val is not None}
+                                         list_block=a.list_block, step_hint=a.step_hint).items()
+               if val is not None}
         if tun:
             s.set_tuning(**tun)
         s.set_state(x, v)

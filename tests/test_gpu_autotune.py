@@ -13,9 +13,10 @@ def test_tuning_does_not_change_results(ljmd, precision):
     x, box = li.perturbed_fcc(3000, 0.8442, 0.08, 501)
     v = li.maxwell_boltzmann(3000, 0.9, 502)
     outs = []
-    for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=0),
-                dict(step_block=64, step_groups=2, list_block=256, list_variant=3),
-                dict(step_block=256, step_groups=2, list_block=64, list_variant=1)]:
+    for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=0, step_hint=0),
+                dict(step_block=64, step_groups=2, list_block=256, list_variant=3, step_hint=1),
+                dict(step_block=256, step_groups=2, list_block=64, list_variant=1, step_hint=1),
+                dict(step_block=128, step_groups=1, list_block=128, list_variant=2, step_hint=1)]:
         with ljmd.LJSystem(box, 3000, 2.5, 0.3, precision) as s:
             s.set_tuning(**tun)
             assert s.get_tuning() == tun
@@ -37,6 +38,7 @@ def test_autotuner_picks_valid_shape(ljmd, tmp_path):
         t = s.get_tuning()
         assert t == res["tuning"]
         assert t["step_block"] in autotune.STEP_BLOCKS and t["step_groups"] in autotune.STEP_GROUPS
+        assert t["step_hint"] in autotune.STEP_HINTS
         again = autotune.tune(s, 0.005, key="t", cache=cache)   # from the cache, no timing
         assert again["tuning"] == res["tuning"]
     with pytest.raises(ljmd.MDError):
