@@ -205,9 +205,13 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
  *   MD_TUNE_STEP_BLOCK   threads per block of the force + integration kernel: 64, 128, 256
  *   MD_TUNE_STEP_GROUPS  FP32-force partners loaded per iteration, in groups of 4: 1, 2
  *   MD_TUNE_LIST_BLOCK   threads per block of the pair-list build: 64, 128, 256
- *   MD_TUNE_LIST_VARIANT pair-list build variant: bit 0 prunes neighbour rows and
- *                        narrows their x windows by the y / z distance to the row,
- *                        bit 1 writes list entries four at a time (0..3)
+ *   MD_TUNE_LIST_VARIANT pair-list build variant (0..4; the lists are identical):
+ *                        0..3 one thread per particle, bit 0 pre-testing candidates
+ *                        on the fixed-point shadow positions instead of positions
+ *                        rounded to float, bit 1 skipping neighbour rows farther
+ *                        than rl in y or z and narrowing the others' x windows;
+ *                        4 warp-cooperative (candidates shared by the lanes of a
+ *                        row, staged in shared memory)
  *   MD_TUNE_STEP_HINT    1: L1 eviction hints on the FP32 step kernel's loads (list
  *                        words not kept in L1, partner positions kept)
  * Defaults 128 / 2 / 128 / 0 / 0. The autotuner (paper_1210_3450_gb300.autotune) times the

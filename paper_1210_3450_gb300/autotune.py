@@ -24,7 +24,7 @@ STEP_BLOCKS = (64, 128, 256)
 STEP_GROUPS = (1, 2)
 STEP_HINTS = (0, 1)
 LIST_BLOCKS = (64, 128, 256)
-LIST_VARIANTS = (0, 1, 2, 3)
+LIST_VARIANTS = (0, 1, 2, 3, 4)
 
 
 def shape_key(precision: int, particles: int, density: float, systems: int) -> str:

@@ -42,6 +42,8 @@ struct SysParams {
   float qunit;       // L / 2^32 as float: fixed-point unit
   float rl2q_lo;     // rl^2 (1 - 1e-5) in fixed-point units^2: certainly inside below
   float rl2q_hi;     // rl^2 (1 + 1e-5) in fixed-point units^2: certainly outside above
+  float rl2f_lo;     // rl^2 (1 - eps(L / rl)) as float: the float pre-test's sure inside
+  float rl2f_hi;     // rl^2 (1 + eps(L / rl)) as float: the float pre-test's sure outside
   float rc2f;        // rc^2 as float (FP32 force cutoff)
   float c2f;         // c2 as float
   float rlf;         // rc + skin as float
@@ -90,6 +92,7 @@ struct DevArrays {
   // rebuild scratch
   double4_32a* xtmp;
   double4_32a* vtmp;
+  float4* xf;         // positions as float at the last list build (list pre-test; 4 spare entries)
   int32_t* idtmp;
   int32_t* celltmp;
   int32_t* perm;      // new slot -> old slot
@@ -111,7 +114,7 @@ struct Tuning {
   int step_block = 128;
   int step_groups = 2;
   int list_block = 128;
-  int list_variant = 0;  // bit 0: row pruning by y / z distance; bit 1: 16-byte list writes
+  int list_variant = 0;  // 0..3 per thread (bit 0: fixed-point pre-test; bit 1: row pruning); 4 per warp
   int step_hint = 0;     // 1: L1 eviction hints on the FP32 step kernel's loads
 };
 

@@ -107,7 +107,7 @@ int Engine::set_tuning(int key, int value) {
       tuning_.list_block = value;
       return kOK;
     case 3:
-      if (value < 0 || value > 3) break;
+      if (value < 0 || value > 4) break;
       tuning_.list_variant = value;
       return kOK;
     case 4:
@@ -271,7 +271,7 @@ int footprint(const SysSpec& s, SysFootprint* f, SysHost* h) {
 void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
-  dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.vtmp); dfree(d_.idtmp);
+  dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.ccount); dfree(d_.cstart);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
@@ -327,9 +327,9 @@ int Engine::alloc_arrays() {
   const int64_t P = caps_.slots, T = caps_.slots / kTile;
   for (int b = 0; b < 2; ++b) {
     CKR(dmalloc(&d_.x[b], P));
-    CKR(dmalloc(&d_.xq[b], P));
+    CKR(dmalloc(&d_.xq[b], P + 4));  // 4 spare entries: the list build reads candidates 4 at a time
     CK(cudaMemset(d_.x[b], 0, sizeof(double4_32a) * P));
-    CK(cudaMemset(d_.xq[b], 0, sizeof(int4) * P));
+    CK(cudaMemset(d_.xq[b], 0, sizeof(int4) * (P + 4)));
   }
   CKR(dmalloc(&d_.v, P));
   CKR(dmalloc(&d_.xref, P));
@@ -341,6 +341,8 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.nbr, caps_.list_words));
   CKR(dmalloc(&d_.tile_obs, 3 * T));
   CKR(dmalloc(&d_.xtmp, P));
+  CKR(dmalloc(&d_.xf, P + 4));
+  CK(cudaMemset(d_.xf, 0, sizeof(float4) * (P + 4)));
   CKR(dmalloc(&d_.vtmp, P));
   CKR(dmalloc(&d_.idtmp, P));
   CKR(dmalloc(&d_.celltmp, P));
@@ -500,6 +502,20 @@ int Engine::upload_params(int only) {
     P.qunit = (float)(h.spec.L / 4294967296.0);
     P.rl2q_lo = (float)(P.rl2 * P.qscale * P.qscale * (1.0 - 1e-5));
     P.rl2q_hi = (float)(P.rl2 * P.qscale * P.qscale * (1.0 + 1e-5));
+    {
+      // Float pre-test of the list build: candidate and key positions rounded to
+      // float (error <= 2^-24 L, key shifted by an image <= 2^-23 L), so each
+      // separation errs by at most e0 = 3 u L (1 + 2^-28) plus u |d|, u = 2^-24.
+      // Near r = rl the float r^2 then errs by less than
+      //   rl^2 (2 sqrt(3) e0 / rl + 3 (e0 / rl)^2 + 6 u e0 / rl + 7 u)
+      // (separation errors, three float roundings, the FP64 test's own roundings,
+      // the thresholds' rounding to float); eps is twice that.
+      const double u = 5.9604644775390625e-08;
+      const double g = 3.0 * u * h.spec.L * (1.0 + 3.7252902984e-09) / h.rl;
+      const double eps = 2.0 * (3.4641016151377544 * g + 3.0 * g * g + 6.0 * u * g + 7.0 * u);
+      P.rl2f_lo = std::nextafter((float)(P.rl2 * (1.0 - eps)), 0.0f);
+      P.rl2f_hi = std::nextafter((float)(P.rl2 * (1.0 + eps)), 3.0e38f);
+    }
     P.rc2f = (float)P.rc2;
     P.c2f = (float)h.c2;
     P.rlf = (float)h.rl;

@@ -230,6 +230,7 @@ __global__ void k_copyback(DevArrays a, int cur) {
   a.xqref[t.s] = q;
   q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
   a.xq[cur][t.s] = q;
+  a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
   a.v[t.s] = a.vtmp[t.s];
   a.id[t.s] = a.idtmp[t.s];
   a.cell[t.s] = a.celltmp[t.s];
@@ -260,99 +261,121 @@ __device__ __forceinline__ unsigned exact_inside(double xi, double yi, double zi
   return code | (r2 < rl2 ? 0x100u : 0u);  // bit 8: inside
 }
 
-struct LBParams {
-  double L, rl2;
-  float rl2q_lo, rl2q_hi;
-  int n;
-};
-
-// List writer: entries are collected four at a time and stored as one 16-byte
-// word group (the list layout keeps a particle's entries 4k..4k+3 adjacent).
-template <bool BUF>
-struct ListOut {
-  uint32_t* out;
+// Per-particle state of the list build. The FP64 position and the system's L and
+// rl^2 are not kept in registers: the rare exact tests reload them.
+struct ListCtx {
+  const SysParams* Pp;
+  const double4_32a* xs;  // FP64 positions of the system
+  uint32_t* out;          // the particle's list words
+  int li;                 // the particle's slot in the system
   int count;
   int kmax;
-  uint4 buf;
-  __device__ __forceinline__ void push(uint32_t e) {
-    if (!BUF) {  // one 4-byte store per entry
-      if (count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
-      ++count;
-      return;
-    }
-    const int slot = count & 3;
-    if (slot == 0) buf.x = e;
-    else if (slot == 1) buf.y = e;
-    else if (slot == 2) buf.z = e;
-    else buf.w = e;
-    if (slot == 3 && count < kmax) *(uint4*)(out + (int64_t)(count >> 2) * (4 * kTile)) = buf;
-    ++count;
+  // Append e when p holds (a predicated store).
+  __device__ __forceinline__ void push_if(bool p, uint32_t e) {
+    if (p && count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
+    count += p ? 1 : 0;
   }
-  __device__ __forceinline__ void flush() {
-    if (BUF && (count & 3) != 0 && count < kmax) *(uint4*)(out + (int64_t)(count >> 2) * (4 * kTile)) = buf;
+  // The exact FP64 test of candidate j with image code (0xff: minimum image).
+  __device__ __forceinline__ void exact(int j, unsigned code) {
+    const double4_32a xi = xs[li], xj = xs[j];
+    const unsigned r = exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, Pp->L, Pp->rl2);
+    push_if((r >> 8) & 1u, (uint32_t)j | ((r & 0xffu) << kIdxBits));
   }
 };
 
-// Append candidate j to the list if it is inside: below rl2q_lo the FP32 bound
-// decides, in the shell (or for per-pair images) the exact FP64 test decides.
-template <class Out>
-__device__ __forceinline__ void accept(const double4_32a* __restrict__ xs, int j, float r2q, unsigned code,
-                                       const double4_32a& xi, const LBParams& P, Out& o) {
-  unsigned cj = code;
-  bool inside = true;
-  if (!(r2q < P.rl2q_lo) || code == 0xffu) {
-    const double4_32a xj = xs[j];
-    const unsigned r = exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, P.L, P.rl2);
-    cj = r & 0xffu;
-    inside = (r >> 8) & 1u;
-  }
-  if (inside) o.push((uint32_t)j | (cj << kIdxBits));
-}
+// Candidate pre-tests: squared distance of candidate j (in this range's image)
+// from the particle, in float, with sure-inside / sure-outside thresholds.
+//   PRE 0: positions rounded to float, key shifted by the range's image;
+//          thresholds rl^2 (1 -/+ eps(L / rl)).
+//   PRE 1: fixed-point shadow positions (the wrapped 32-bit difference is the
+//          minimum image) converted to float; thresholds rl^2 (1 -/+ 1e-5) in
+//          fixed-point units (relative error of r^2 below 3.2e-6 for L <= 10^4).
+template <int PRE>
+struct PreTest;
 
-__device__ __forceinline__ float r2_fixed(const int4& qj, const int4& qi) {
-  const float ax = (float)wrapped_diff(qj.x, qi.x);
-  const float ay = (float)wrapped_diff(qj.y, qi.y);
-  const float az = (float)wrapped_diff(qj.z, qi.z);
-  return fmaf(az, az, fmaf(ay, ay, ax * ax));
-}
-
-// Test the candidates of slot range [lo, hi) (all with image `code`, or 0xff for
-// the per-pair minimum image) against particle li and append the partners, in
-// candidate order. With `sorted`, the range is ordered by x (key: float x in q.w)
-// and only the window xlo <= x_j < xhi can hold partners (|dx| < rl, bounds
-// widened by a margin): the first candidate is found by bisection and the sweep
-// stops past xhi. Candidates are taken four at a time (independent loads,
-// straight-line tests); the rare accepted ones take the slow path in order.
-template <class Out>
-__device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const double4_32a* __restrict__ xs,
-                                            int lo, int hi, unsigned code, int li, const int4& qi,
-                                            const double4_32a& xi, const LBParams& P, Out& o,
-                                            bool sorted, float xlo, float xhi) {
-  if (sorted) {
-    int b = hi;
-    while (lo < b) {
-      const int m = (lo + b) >> 1;
-      if (__int_as_float(qs[m].w) < xlo) lo = m + 1;
-      else b = m;
-    }
+template <>
+struct PreTest<0> {
+  const float4* p;
+  float cx, cy, cz;  // the particle's position minus the image shift
+  float lo2, hi2;
+  __device__ __forceinline__ float key(int j) const { return p[j].x; }
+  __device__ __forceinline__ float r2(const float4& q) const {
+    const float dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
   }
+  __device__ __forceinline__ float4 load(int j) const { return p[j]; }
+};
+
+template <>
+struct PreTest<1> {
+  const int4* p;
+  int qx, qy, qz;
+  float lo2, hi2;
+  __device__ __forceinline__ float key(int j) const { return __int_as_float(p[j].w); }
+  __device__ __forceinline__ float r2(const int4& q) const {
+    const float ax = (float)wrapped_diff(q.x, qx);
+    const float ay = (float)wrapped_diff(q.y, qy);
+    const float az = (float)wrapped_diff(q.z, qz);
+    return fmaf(az, az, fmaf(ay, ay, ax * ax));
+  }
+  __device__ __forceinline__ int4 load(int j) const { return p[j]; }
+};
+
+__device__ __forceinline__ float key_of(const float4& q) { return q.x; }
+__device__ __forceinline__ float key_of(const int4& q) { return __int_as_float(q.w); }
+
+// Test the candidates of slot range [lo, hi), all with image `code`, against the
+// particle and append the partners in candidate order. The range is ordered by x
+// (float key) and only the window xlo <= x_j < xhi can hold partners: the first
+// candidate is found by bisection and the sweep stops past xhi. Candidates are
+// taken four at a time (independent loads; the slot arrays have four spare
+// entries, masked off, at the end); when the pre-test decides all four the
+// appends are predicated stores, otherwise the four take the exact test in order.
+template <int PRE>
+__device__ __forceinline__ void sweep_range(const PreTest<PRE>& T, ListCtx& o, int lo, int hi, unsigned code,
+                                            float xlo, float xhi) {
+  int b = hi;
+  while (lo < b) {
+    const int m = (lo + b) >> 1;
+    if (T.key(m) < xlo) lo = m + 1;
+    else b = m;
+  }
+  const uint32_t cbits = code << kIdxBits;
   for (int j = lo; j < hi; j += 4) {
-    const int4 q0 = qs[j];
-    const int4 q1 = j + 1 < hi ? qs[j + 1] : q0;
-    const int4 q2 = j + 2 < hi ? qs[j + 2] : q0;
-    const int4 q3 = j + 3 < hi ? qs[j + 3] : q0;
-    if (sorted && !(__int_as_float(q0.w) < xhi)) break;
-    const float r0 = r2_fixed(q0, qi), r1 = r2_fixed(q1, qi), r2 = r2_fixed(q2, qi), r3 = r2_fixed(q3, qi);
-    unsigned m = (r0 < P.rl2q_hi ? 1u : 0u) | (r1 < P.rl2q_hi ? 2u : 0u) | (r2 < P.rl2q_hi ? 4u : 0u) |
-                 (r3 < P.rl2q_hi ? 8u : 0u);
+    const auto q0 = T.load(j), q1 = T.load(j + 1), q2 = T.load(j + 2), q3 = T.load(j + 3);
+    if (!(key_of(q0) < xhi)) break;
+    const float r0 = T.r2(q0), r1 = T.r2(q1), r2 = T.r2(q2), r3 = T.r2(q3);
+    unsigned m = (r0 < T.hi2 ? 1u : 0u) | (r1 < T.hi2 ? 2u : 0u) | (r2 < T.hi2 ? 4u : 0u) | (r3 < T.hi2 ? 8u : 0u);
     m &= (hi - j) >= 4 ? 15u : ((1u << (hi - j)) - 1u);
-    if ((unsigned)(li - j) < 4u) m &= ~(1u << (li - j));  // not the particle itself
+    if ((unsigned)(o.li - j) < 4u) m &= ~(1u << (o.li - j));  // not the particle itself
     if (m) {
-      if (m & 1u) accept(xs, j, r0, code, xi, P, o);
-      if (m & 2u) accept(xs, j + 1, r1, code, xi, P, o);
-      if (m & 4u) accept(xs, j + 2, r2, code, xi, P, o);
-      if (m & 8u) accept(xs, j + 3, r3, code, xi, P, o);
+      const unsigned in = m & ((r0 < T.lo2 ? 1u : 0u) | (r1 < T.lo2 ? 2u : 0u) | (r2 < T.lo2 ? 4u : 0u) |
+                               (r3 < T.lo2 ? 8u : 0u));
+      if (in == m) {
+        const uint32_t e = (uint32_t)j | cbits;
+        o.push_if(m & 1u, e);
+        o.push_if(m & 2u, e + 1);
+        o.push_if(m & 4u, e + 2);
+        o.push_if(m & 8u, e + 3);
+      } else {
+        for (int k = 0; k < 4; ++k)
+          if ((m >> k) & 1u) o.exact(j + k, code);
+      }
     }
+  }
+}
+
+// nc == 1: every particle is a candidate. The fixed-point separation (its wrapped
+// difference is the minimum image) rules out the far ones; the rest take the exact
+// minimum-image test.
+__device__ __forceinline__ void sweep_all(ListCtx& o, const int4* __restrict__ q, float hi2, int n) {
+  const int4 qi = q[o.li];
+  for (int j = 0; j < n; ++j) {
+    const int4 qj = q[j];
+    const float ax = (float)wrapped_diff(qj.x, qi.x);
+    const float ay = (float)wrapped_diff(qj.y, qi.y);
+    const float az = (float)wrapped_diff(qj.z, qi.z);
+    if (j != o.li && fmaf(az, az, fmaf(ay, ay, ax * ax)) < hi2) o.exact(j, 0xffu);
   }
 }
 
@@ -360,22 +383,114 @@ __device__ __forceinline__ void sweep_range(const int4* __restrict__ qs, const d
 
 // Full list: every j != i with minimum-image r^2 < rl^2 (strict); one thread per
 // particle, candidates from the 27 neighbour cells taken as 9 rows of 3 cells that
-// are contiguous in cell order (split in two where a row wraps), or from all
+// are contiguous in cell order (split in two where a row wraps in x), or from all
 // particles when nc == 1. Partners are appended in candidate order
-// (deterministic).
+// (deterministic, and the same for every PRE).
 //
 // The decision is the FP64 test ((dx dx + dy dy) + dz dz < rl^2, no fused
-// operations). It is taken first from the fixed-point separation in FP32, whose
-// relative error on r^2 is below 3.2e-6 for L <= 10^4 (quantisation <= 1 unit per
-// axis, at least 1.2e6 units per rl; five FP32 roundings): below rl^2 (1 - 1e-5)
-// the pair is certainly inside, above rl^2 (1 + 1e-5) certainly outside, and only
-// the thin shell between needs the FP64 test. The result is identical to always
-// taking it.
-// VAR bit 0: prune rows and narrow x windows by the y / z distance to the row;
-// VAR bit 1: write entries four at a time. Chosen by the autotuner.
+// operations). It is taken first by a float pre-test whose error is bounded: below
+// its lower threshold the pair is certainly inside, above the upper one certainly
+// outside, and only the thin shell between needs the FP64 test. The result is
+// identical to always taking it.
+// VAR bit 0: the fixed-point pre-test (else float); bit 1: rows farther than rl
+// in y or z are skipped and the x window of each row is narrowed to
+// sqrt(rl^2 - dy^2 - dz^2) (dy, dz: distances from the particle to the row).
+namespace {
+
+// The 9 neighbour rows of one particle (cells other than nc == 1), swept by
+// its own thread.
+template <int PRE, bool kPrune>
+__device__ __forceinline__ void lane_rows(const DevArrays& a, int cur, const SysParams* __restrict__ Pp, ListCtx& o,
+                                          int64_t p_off) {
+  const int li = o.li, nc = Pp->nc;
+  const double4_32a xi0 = o.xs[li];
+  const float rl = Pp->rlf, wm = Pp->wmargin;
+  float w = rl + wm;  // half-width of the x window
+  PreTest<PRE> T;
+  if constexpr (PRE == 0) {
+    T.p = a.xf + p_off;
+    T.lo2 = Pp->rl2f_lo;
+    T.hi2 = Pp->rl2f_hi;
+  } else {
+    T.p = a.xq[cur] + p_off;
+    const int4 qi = T.p[li];
+    T.qx = qi.x; T.qy = qi.y; T.qz = qi.z;
+    T.lo2 = Pp->rl2q_lo;
+    T.hi2 = Pp->rl2q_hi;
+  }
+  const int32_t* cst = a.cstart + Pp->c_off;
+  const int ci = a.cell[p_off + li];
+  const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
+  const int nparts = (cx == 0 || cx == nc - 1) ? 2 : 1;
+  const double L = Pp->L;
+  // offsets of the particle from its cell's lower y and z faces (row pruning)
+  const float cs = Pp->csf;
+  const float fy = kPrune ? (float)xi0.y - (float)cy * cs : 0.f;
+  const float fz = kPrune ? (float)xi0.z - (float)cz * cs : 0.f;
+#pragma unroll 1
+  for (int rowi = 0; rowi < 9; ++rowi) {
+    const int oz = rowi / 3 - 1, oy = rowi % 3 - 1;
+    if (kPrune) {
+      // the margin (1e-5 L) is far above the float rounding of x_i and of the
+      // cell faces (about 1e-7 L)
+      const float dy = fmaxf(0.f, (oy < 0 ? fy : (oy > 0 ? cs - fy : 0.f)) - wm);
+      const float dz = fmaxf(0.f, (oz < 0 ? fz : (oz > 0 ? cs - fz : 0.f)) - wm);
+      const float rem = rl * rl - dy * dy - dz * dz;
+      if (rem <= 0.f) continue;  // the whole row is farther than rl
+      w = sqrtf(rem) + wm;
+    }
+    int nz = cz + oz, ny = cy + oy;
+    unsigned shz = 0, shy = 0;
+    if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
+    if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
+    const int row = nc * (ny + nc * nz);
+    const double4_32a xi = o.xs[li];  // reloaded (an L1 hit) rather than held in registers
+    if constexpr (PRE == 0) {
+      // image code 1 adds +L to x_j - x_i, code 2 adds -L: shift the particle instead
+      T.cy = (float)(shy == 1 ? xi.y - L : (shy == 2 ? xi.y + L : xi.y));
+      T.cz = (float)(shz == 1 ? xi.z - L : (shz == 2 ? xi.z + L : xi.z));
+    }
+#pragma unroll 1
+    for (int part = 0; part < nparts; ++part) {
+      int lo, hi;
+      unsigned code = (shy << 2) | (shz << 4);
+      // cells cx-1..cx+1 of this row: one contiguous range, or two where it wraps
+      if (cx == 0) {
+        if (part == 0) { lo = cst[row + nc - 1]; hi = cst[row + nc]; code |= 2u; }  // x image -L
+        else { lo = cst[row]; hi = cst[row + 2]; }
+      } else if (cx == nc - 1) {
+        if (part == 0) { lo = cst[row + nc - 2]; hi = cst[row + nc]; }
+        else { lo = cst[row]; hi = cst[row + 1]; code |= 1u; }                    // x image +L
+      } else {
+        lo = cst[row + cx - 1]; hi = cst[row + cx + 2];
+      }
+      // the particle's x in this range's coordinates (candidates are not shifted)
+      const double xs_ = (code & 3u) == 1u ? xi.x - L : ((code & 3u) == 2u ? xi.x + L : xi.x);
+      const float xw = (float)xs_;
+      if constexpr (PRE == 0) T.cx = xw;
+      sweep_range<PRE>(T, o, lo, hi, code, xw - w, xw + w);
+    }
+  }
+}
+
+// List length, the system's largest length and overflow (one atomic per warp:
+// all threads of a system hitting one word serialise).
+__device__ __forceinline__ void list_done(const DevArrays& a, int sys, int64_t slot, int count, int kmax,
+                                          bool act, unsigned mask, int lane) {
+  if (act) a.ncnt[slot] = count < kmax ? count : kmax;
+  const int wmax = __reduce_max_sync(mask, act ? count : 0);
+  if (lane == __ffs(mask) - 1) {
+    atomicMax(&a.status[sys].max_count, wmax);
+    if (wmax > kmax) atomicMax(&a.status[sys].overflow, wmax);
+  }
+}
+
+}  // namespace
+
 template <int BLOCK, int VAR>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a, int cur) {
-  constexpr bool kPrune = (VAR & 1) != 0;
+  constexpr int PRE = VAR & 1;
+  constexpr bool kPrune = (VAR & 2) != 0;
   const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= a.ntiles) return;
@@ -385,82 +500,159 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
   if (!Pp->active) return;
   const int tl = warp - Pp->t_off;
   const int li = tl * kTile + lane;
-  if (li >= Pp->n) return;
+  const int n = Pp->n;
+  if (li >= n) return;
   const int64_t p_off = Pp->p_off;
-  const double4_32a* xs = a.x[cur] + p_off;
-  const int4* qs = a.xq[cur] + p_off;
-  const double4_32a xi = xs[li];
-  const int4 qi = qs[li];
-  LBParams P{Pp->L, Pp->rl2, Pp->rl2q_lo, Pp->rl2q_hi, Pp->n};
-  // Geometric windows: a partner in a row with offsets (oy, oz) is at least
-  // dy_min, dz_min away in y and z (distance of x_i to its cell's faces), so its
-  // x separation is below sqrt(rl^2 - dy_min^2 - dz_min^2); rows where that is
-  // negative are skipped. The margin (1e-5 L) is far above the float rounding of
-  // the keys and of the cell faces (about 1e-7 L).
-  const float rl = Pp->rlf, cs = Pp->csf, wm = Pp->wmargin;
-  ListOut<(VAR & 2) != 0> o{a.nbr + list_word(Pp->l_off, tl, Pp->kmax, lane, 0), 0, Pp->kmax, make_uint4(0, 0, 0, 0)};
+  const int kmax = Pp->kmax;
+  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax};
+  if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+  else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
+  list_done(a, sys, p_off + li, o.count, kmax, true, __activemask(), lane);
+}
+
+// Warp-cooperative list build: the same lists, in the same order, as
+// k_build_list. The lanes of a warp that share a row of cells (y, z) take the
+// union of their candidates: for each of the 9 neighbour rows, the cells
+// cx_min-1 .. cx_max+1 restricted to the group's x window, read 32 at a time with
+// coalesced loads into shared memory and tested by every lane from there
+// (broadcast reads). Each lane collects its accepted candidates of a chunk in a
+// bit mask (pre-test; the shell resolved by the exact FP64 test) and appends them
+// in candidate order. Candidates outside a lane's own three cells are farther
+// than the cell side >= rl, so they fail its test; every cell of the union
+// appears once, with one image, because a group spans at most nc - 2 cells
+// (wider runs of a row are split into several groups).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArrays a, int cur) {
+  __shared__ float4 sbuf[BLOCK];
+  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.ntiles) return;  // every return above the loop is uniform over the warp
+  const int sys = a.tile_sys[warp];
+  if (sys < 0 || !a.rebuild[sys]) return;
+  const SysParams* __restrict__ Pp = a.params + sys;
+  if (!Pp->active) return;
+  const int tl = warp - Pp->t_off;
+  const int li = tl * kTile + lane;
+  const int n = Pp->n;
+  const bool act = li < n;
+  const unsigned actm = __ballot_sync(kFull, act);
+  const int64_t p_off = Pp->p_off;
+  const int kmax = Pp->kmax;
+  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax};
   const int nc = Pp->nc;
-  const int32_t* cst = a.cstart + Pp->c_off;
-  int cx = 0, cy = 0, cz = 0;
-  float fy = 0.f, fz = 0.f;  // offsets of x_i from its cell's lower faces
-  if (nc > 1) {
-    const int ci = a.cell[p_off + li];
-    cx = ci % nc; cy = (ci / nc) % nc; cz = ci / (nc * nc);
-    fy = (float)xi.y - (float)cy * cs;
-    fz = (float)xi.z - (float)cz * cs;
+  if (nc == 1) {
+    if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+    list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+    return;
   }
-  // 9 rows of the 27-cell block (2 ranges each at most), or one range of all
-  // particles when nc == 1
-  const int nseg = nc > 1 ? 18 : 1;
+  float4* buf = sbuf + (threadIdx.x & ~31);
+  const float4* __restrict__ xf = a.xf + p_off;
+  const int32_t* __restrict__ cst = a.cstart + Pp->c_off;
+  const double L = Pp->L;
+  const float w = Pp->rlf + Pp->wmargin;  // half-width of the x window around each particle
+  const float lo2 = Pp->rl2f_lo, hi2 = Pp->rl2f_hi;
+  int cx = 0, rkey = -1;
+  float xk = 0.f;
+  if (act) {
+    const int ci = a.cell[p_off + li];
+    cx = ci % nc;
+    rkey = ci / nc;  // row of cells (y, z)
+    xk = xf[li].x;
+  }
+  unsigned todo = actm;
+  while (todo) {
+    // next group: the remaining lanes of one row whose cells span at most nc - 2
+    // (so that the union of their neighbour cells holds each cell once)
+    const int gkey = __shfl_sync(kFull, rkey, __ffs(todo) - 1);
+    const bool same = ((todo >> lane) & 1u) && rkey == gkey;
+    const int cxa = __reduce_min_sync(kFull, same ? cx : 0x7fffffff);
+    const unsigned grp = __ballot_sync(kFull, same && cx <= cxa + nc - 3);
+    todo &= ~grp;
+    const bool mine = (grp >> lane) & 1u;
+    const int cxb = __reduce_max_sync(kFull, mine ? cx : -1);
+    // x extent of the group: x >= 0, so the float bits order like the values
+    const float xmin = __int_as_float(__reduce_min_sync(kFull, mine ? __float_as_int(xk) : 0x7f800000));
+    const float xmax = __int_as_float(__reduce_max_sync(kFull, mine ? __float_as_int(xk) : 0));
+    const int gcy = gkey % nc, gcz = gkey / nc;
+    const int npieces = (cxa == 0 || cxb == nc - 1) ? 2 : 1;
 #pragma unroll 1
-  for (int seg = 0; seg < nseg; ++seg) {
-    int lo, hi;
-    unsigned code;
-    float w = rl + wm;  // half-width of the x window
-    if (nc > 1) {
-      const int rowi = seg >> 1, part = seg & 1;
+    for (int rowi = 0; rowi < 9; ++rowi) {
       const int oz = rowi / 3 - 1, oy = rowi % 3 - 1;
-      if (kPrune) {
-        const float dy = fmaxf(0.f, (oy < 0 ? fy : (oy > 0 ? cs - fy : 0.f)) - wm);
-        const float dz = fmaxf(0.f, (oz < 0 ? fz : (oz > 0 ? cs - fz : 0.f)) - wm);
-        const float rem = rl * rl - dy * dy - dz * dz;
-        if (rem <= 0.f) continue;  // the whole row is farther than rl
-        w = sqrtf(rem) + wm;
-      }
-      int nz = cz + oz, ny = cy + oy;
+      int nz = gcz + oz, ny = gcy + oy;
       unsigned shz = 0, shy = 0;
       if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
       if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
       const int row = nc * (ny + nc * nz);
-      code = (shy << 2) | (shz << 4);
-      // cells cx-1..cx+1 of this row: one contiguous range, or two where it wraps
-      if (cx == 0) {
-        if (part == 0) { lo = cst[row + nc - 1]; hi = cst[row + nc]; code |= 2u; }  // x image -L
-        else { lo = cst[row]; hi = cst[row + 2]; }
-      } else if (cx == nc - 1) {
-        if (part == 0) { lo = cst[row + nc - 2]; hi = cst[row + nc]; }
-        else { lo = cst[row]; hi = cst[row + 1]; code |= 1u; }                    // x image +L
-      } else {
-        if (part == 0) { lo = cst[row + cx - 1]; hi = cst[row + cx + 2]; }
-        else { lo = 0; hi = 0; }
+      const double4_32a xi = o.xs[li];  // padding lanes read their zeroed slot
+      // image code 1 adds +L to x_j - x_i, code 2 adds -L: shift the particle instead
+      const float cy = (float)(shy == 1 ? xi.y - L : (shy == 2 ? xi.y + L : xi.y));
+      const float cz = (float)(shz == 1 ? xi.z - L : (shz == 2 ? xi.z + L : xi.z));
+#pragma unroll 1
+      for (int piece = 0; piece < npieces; ++piece) {
+        int c0, c1;  // first and last cell of this piece (contiguous in cell order)
+        unsigned code = (shy << 2) | (shz << 4);
+        if (cxa == 0) {
+          if (piece == 0) { c0 = c1 = nc - 1; code |= 2u; }  // x image -L
+          else { c0 = 0; c1 = cxb + 1; }
+        } else if (cxb == nc - 1) {
+          if (piece == 0) { c0 = cxa - 1; c1 = nc - 1; }
+          else { c0 = c1 = 0; code |= 1u; }                  // x image +L
+        } else {
+          c0 = cxa - 1; c1 = cxb + 1;
+        }
+        int lo = cst[row + c0];
+        const int hi = cst[row + c1 + 1];
+        const float sx = (code & 3u) == 1u ? -(float)L : ((code & 3u) == 2u ? (float)L : 0.f);
+        const float xlo = xmin + sx - w, xhi = xmax + sx + w;
+        const float cxf = (float)((code & 3u) == 1u ? xi.x - L : ((code & 3u) == 2u ? xi.x + L : xi.x));
+        // first candidate of the window (every lane takes the same steps)
+        int b = hi;
+        while (lo < b) {
+          const int m = (lo + b) >> 1;
+          if (xf[m].x < xlo) lo = m + 1;
+          else b = m;
+        }
+        const uint32_t cbits = code << kIdxBits;
+        for (int j0 = lo; j0 < hi; j0 += 32) {
+          const int j = j0 + lane;
+          const float4 q = j < hi ? xf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const unsigned vm = __ballot_sync(kFull, j < hi && q.x < xhi);  // a prefix: keys ascend
+          if (vm == 0) break;
+          buf[lane] = q;
+          __syncwarp();
+          if (mine) {
+            unsigned M = 0, C = 0;  // maybe inside (below hi2), certainly inside (below lo2)
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const float4 c = buf[t];
+              const float dx = c.x - cxf, dy = c.y - cy, dz = c.z - cz;
+              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              M |= r2 < hi2 ? 1u << t : 0u;
+              C |= r2 < lo2 ? 1u << t : 0u;
+            }
+            M &= vm;
+            if ((unsigned)(li - j0) < 32u) M &= ~(1u << (li - j0));  // not the particle itself
+            C &= M;
+            unsigned S = M & ~C;  // in the shell: the exact test decides (rare)
+            while (S) {
+              const int t = __ffs(S) - 1;
+              S &= S - 1;
+              const double4_32a xa = o.xs[li], xj = o.xs[j0 + t];
+              if (exact_inside(xa.x, xa.y, xa.z, xj.x, xj.y, xj.z, code, L, Pp->rl2) & 0x100u) C |= 1u << t;
+            }
+            while (C) {
+              const int t = __ffs(C) - 1;
+              C &= C - 1;
+              o.push_if(true, (uint32_t)(j0 + t) | cbits);
+            }
+          }
+          __syncwarp();
+          if (vm != kFull) break;
+        }
       }
-    } else {
-      lo = 0; hi = P.n; code = 0xffu;
     }
-    // x window of the candidates in this range's own coordinates
-    const float sx = (code & 3u) == 2u ? (float)Pp->L : ((code & 3u) == 1u ? -(float)Pp->L : 0.0f);
-    const float xw = (float)xi.x + sx;
-    sweep_range(qs, xs, lo, hi, code, li, qi, xi, P, o, nc > 1, xw - w, xw + w);
   }
-  o.flush();
-  a.ncnt[p_off + li] = o.count < o.kmax ? o.count : o.kmax;
-  // one atomic per warp (all threads of a system hitting one word serialise)
-  const unsigned act = __activemask();
-  const int wmax = __reduce_max_sync(act, o.count);
-  if (lane == __ffs(act) - 1) {
-    atomicMax(&a.status[sys].max_count, wmax);
-    if (wmax > o.kmax) atomicMax(&a.status[sys].overflow, wmax);
-  }
+  list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
 }
 
 // ------------------------------------- fused force + velocity-Verlet step
@@ -881,6 +1073,13 @@ static void launch_build_list_v(const DevArrays& a, int cur, int block, cudaStre
 
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s) {
   switch (tu.list_variant) {
+    case 4:
+      switch (tu.list_block) {
+        case 64: k_build_list_warp<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
+        case 256: k_build_list_warp<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
+        default: k_build_list_warp<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+      }
+      break;
     case 1: launch_build_list_v<1>(a, cur, tu.list_block, s); break;
     case 2: launch_build_list_v<2>(a, cur, tu.list_block, s); break;
     case 3: launch_build_list_v<3>(a, cur, tu.list_block, s); break;

@@ -33,6 +33,7 @@ def main(argv=None):
     p.add_argument("--step-groups", type=int, default=None)
     p.add_argument("--list-block", type=int, default=None)
     p.add_argument("--step-hint", type=int, default=None)
+    p.add_argument("--list-variant", type=int, default=None)
     p.add_argument("--autotune", action="store_true")
     a = p.parse_args(argv)
     import lj_inputs as li
@@ -46,7 +47,8 @@ def main(argv=None):
     mode = MD_FP32_FORCE if a.precision == "fp32" else MD_FP64
     with LJSystem(box, n, a.rc, a.skin, mode) as s:
         tun = {k: val for k, val in dict(step_block=a.step_block, step_groups=a.step_groups,
-                                         list_block=a.list_block, step_hint=a.step_hint).items()
+                                         list_block=a.list_block, step_hint=a.step_hint,
+                                         list_variant=a.list_variant).items()
                if val is not None}
         if tun:
             s.set_tuning(**tun)

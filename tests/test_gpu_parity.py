@@ -72,10 +72,44 @@ LIST_CONFIGS = CONFIGS + [("uniform-3000", _U, 18.0)]
 LIST_IDS = IDS + ["uniform-3000"]
 
 
+def shell_pairs(count=2000, box=300.0, rl=2.8, seed=11):
+    """Pairs at distances rl (1 + t), t uniform within three times the widest
+    pre-test shell (a few 1e-4 at this L / rl), a fifth of them straddling a
+    box face: most pairs fall between the pre-tests' sure-inside and
+    sure-outside thresholds, on both sides of rl."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.0, box, size=(count, 3))
+    c[: count // 5, rng.integers(0, 3)] = rng.uniform(0.0, 1.0, size=count // 5)
+    u = rng.normal(size=(count, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    t = rng.uniform(-4e-4, 4e-4, size=(count, 1))
+    return np.concatenate([c, c + rl * (1.0 + t) * u]), box
+
+
+_S = shell_pairs()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4],
+                         ids=["float", "fixed", "float-pruned", "fixed-pruned", "warp"])
+def test_list_bit_exact_in_the_shell(ljmd, oracle, variant):
+    x, box = _S
+    with make(ljmd, x, np.zeros_like(x), box) as s:
+        s.set_tuning(list_variant=variant)
+        s.build_list()
+        xw = oracle.wrap(x, box)
+        start, partners = s.get_list()
+        ostart, opartners = oracle.build_list(xw, box, 2.8)
+        assert ostart[-1] > 1000          # many pairs inside, many just outside
+        np.testing.assert_array_equal(start, ostart)
+        np.testing.assert_array_equal(sorted_csr(start, partners), opartners)
+
+
+@pytest.mark.parametrize("variant", [0, 4], ids=["lane", "warp"])
 @pytest.mark.parametrize("name,x,box", LIST_CONFIGS, ids=LIST_IDS)
-def test_wrap_cells_and_list_bit_exact(ljmd, oracle, name, x, box):
+def test_wrap_cells_and_list_bit_exact(ljmd, oracle, name, x, box, variant):
     v = np.zeros_like(x)
     with make(ljmd, x, v, box) as s:
+        s.set_tuning(list_variant=variant)
         s.build_list()
         xg, _ = s.get_state()
         xw = oracle.wrap(x, box)
