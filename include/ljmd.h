@@ -214,13 +214,20 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
  *                        row, staged in shared memory)
  *   MD_TUNE_STEP_HINT    1: L1 eviction hints on the FP32 step kernel's loads (list
  *                        words not kept in L1, partner positions kept)
- * Defaults 128 / 2 / 128 / 0 / 0. The autotuner (paper_1210_3450_gb300.autotune) times the
+ *   MD_TUNE_GRAPH        1: md_step runs its steps in CUDA-graph launches (a loop node of
+ *                        two steps, each followed by a device-side list-validity
+ *                        decision and a conditional rebuild pass), reading the
+ *                        control words once per launch; 0: the host decides after
+ *                        every step. Results are identical. Timing (md_set_timing)
+ *                        uses the host-driven loop.
+ * Defaults 128 / 2 / 128 / 0 / 1 / 1. The autotuner (paper_1210_3450_gb300.autotune) times the
  * choices on the caller's own systems and sets the fastest. */
 #define MD_TUNE_STEP_BLOCK 0
 #define MD_TUNE_STEP_GROUPS 1
 #define MD_TUNE_LIST_BLOCK 2
 #define MD_TUNE_LIST_VARIANT 3
 #define MD_TUNE_STEP_HINT 4
+#define MD_TUNE_GRAPH 5
 MD_API int md_set_tuning(md_ctx* ctx, int key, int value);
 MD_API int md_get_tuning(md_ctx* ctx, int key, int* value);
 

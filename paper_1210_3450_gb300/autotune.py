@@ -81,8 +81,8 @@ def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None 
             list_times[(lb, lv)] = t["list_ms"] / t["list_launches"]
     lbest, lvar = min(list_times, key=list_times.get) if list_times else (128, 0)
     system.set_tuning(list_block=lbest, list_variant=lvar)
-    out = dict(tuning=dict(step_block=blk, step_groups=grp, step_hint=hint, list_block=lbest,
-                           list_variant=lvar),
+    system.set_timing(False)
+    out = dict(tuning=system.get_tuning(),
                step_ms=results, list_ms={f"{k[0]}v{k[1]}": v for k, v in list_times.items()})
     if cache and key:
         data = _load(cache)

@@ -46,6 +46,8 @@ struct SysParams {
   float rl2f_hi;     // rl^2 (1 + eps(L / rl)) as float: the float pre-test's sure outside
   float rc2f;        // rc^2 as float (FP32 force cutoff)
   float c2f;         // c2 as float
+  double skin;       // list margin (validity rule 2 d_max >= skin)
+  double disp_thr;   // FP32-force form: threshold of the squared fixed-point displacement
   float rlf;         // rc + skin as float
   float csf;         // cell side L / nc as float
   float wmargin;     // margin of the list build's geometric windows (1e-5 L + 1e-6)
@@ -77,6 +79,18 @@ enum StepFlags : int {
   kStepKickB = 16,      // v += dt/2 F, first half-kick of the next step
 };
 
+// Control words of the graph-captured step loop (device-resident; NULL in
+// DevArrays when the host drives the loop).
+struct GraphCtl {
+  int32_t abort;   // 1: a pair list overflowed, 2: a non-finite value; the remaining steps do nothing
+  int32_t flags;   // StepFlags of the next step
+  int32_t nreb;    // systems rebuilding in the current pass
+  int32_t done;    // steps taken
+  int32_t target;  // steps to take
+  int32_t passes;  // rebuild passes taken
+  int32_t pad_[2];
+};
+
 struct DevArrays {
   double4_32a* x[2];      // positions (w unused), ping-pong by step parity
   double4_32a* v;         // velocities
@@ -106,6 +120,7 @@ struct DevArrays {
   const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
   const int32_t* tile_sys;  // system of each global tile
   int32_t ntiles;
+  GraphCtl* ctl;            // graph-captured loop: step flags, rebuild count, abort word
 };
 
 // Launch shapes of the hot kernels (threads per block; partner groups of four
@@ -115,7 +130,7 @@ struct Tuning {
   int step_groups = 2;
   int list_block = 128;
   int list_variant = 0;  // 0..3 per thread (bit 0: fixed-point pre-test; bit 1: row pruning); 4 per warp
-  int step_hint = 0;     // 1: L1 eviction hints on the FP32 step kernel's loads
+  int step_hint = 1;     // 1: L1 eviction hints on the FP32 step kernel's loads
 };
 
 // ---------------------------------------------------------------- launchers
@@ -129,6 +144,10 @@ void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, 
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
+// Device-side list-validity decision of the graph-captured loop (see GraphCtl).
+void launch_decide(const DevArrays& a, int nsys, int fp32, int32_t* rebuild, int32_t* rebuild_ids,
+                   int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
+                   int last, cudaStream_t s);
 // mode 0: FP64 reciprocal; 1..4: approximate reciprocal of Sec. 3.3 (8 bits,
 // 8 bits corrected, 23 bits, 23 bits corrected)
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,

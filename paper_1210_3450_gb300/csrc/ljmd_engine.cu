@@ -88,6 +88,8 @@ const char* last_error_cstr() { return g_err.c_str(); }
 
 Engine::~Engine() {
   free_all();
+  for (cudaStream_t& c : cap_)
+    if (c) { cudaStreamDestroy(c); c = nullptr; }
   for (cudaEvent_t e : ev_free_) cudaEventDestroy(e);
   for (TimedPair& p : ev_pending_) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
 }
@@ -97,22 +99,31 @@ int Engine::set_tuning(int key, int value) {
     case 0:
       if (value != 64 && value != 128 && value != 256) break;
       tuning_.step_block = value;
+      ++struct_ver_;
       return kOK;
     case 1:
       if (value != 1 && value != 2) break;
       tuning_.step_groups = value;
+      ++struct_ver_;
       return kOK;
     case 2:
       if (value != 64 && value != 128 && value != 256) break;
       tuning_.list_block = value;
+      ++struct_ver_;
       return kOK;
     case 3:
       if (value < 0 || value > 4) break;
       tuning_.list_variant = value;
+      ++struct_ver_;
       return kOK;
     case 4:
       if (value != 0 && value != 1) break;
       tuning_.step_hint = value;
+      ++struct_ver_;
+      return kOK;
+    case 5:
+      if (value != 0 && value != 1) break;
+      graph_ = value != 0;
       return kOK;
     default:
       break;
@@ -123,7 +134,7 @@ int Engine::set_tuning(int key, int value) {
 
 int Engine::get_tuning(int key) const {
   return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block
-         : key == 3 ? tuning_.list_variant : key == 4 ? tuning_.step_hint : -1;
+         : key == 3 ? tuning_.list_variant : key == 4 ? tuning_.step_hint : key == 5 ? (graph_ ? 1 : 0) : -1;
 }
 
 int Engine::set_timing(bool on) {
@@ -276,6 +287,8 @@ void Engine::free_all() {
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_);
+  drop_graphs();
+  dfree(d_ctl_); dfree(d_reb_count_); hfree(h_ctl_); hfree(h_reb_count_);
   d_ = DevArrays{};
   stage_n_ = 0;
 }
@@ -371,6 +384,12 @@ int Engine::alloc_arrays() {
   CK(cudaMallocHost((void**)&h_disp2_, sizeof(unsigned long long) * ns));
   CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * 2 * ns));
   CK(cudaMallocHost((void**)&h_obs_, sizeof(double) * 3 * ns));
+  CKR(dmalloc(&d_ctl_, 1));
+  CKR(dmalloc(&d_reb_count_, ns));
+  CK(cudaMemset(d_ctl_, 0, sizeof(GraphCtl)));
+  CK(cudaMallocHost((void**)&h_ctl_, sizeof(GraphCtl)));
+  CK(cudaMallocHost((void**)&h_reb_count_, sizeof(int32_t) * ns));
+  ++struct_ver_;
   return upload_params();
 }
 
@@ -394,6 +413,7 @@ void Engine::update_extent() {
     max_cells_ = std::max(max_cells_, h.ncell);
   }
   ntiles_ = last;
+  ++struct_ver_;
 }
 
 int Engine::grow_list_arena(int64_t min_extra_units) {
@@ -406,6 +426,7 @@ int Engine::grow_list_arena(int64_t min_extra_units) {
   d_.nbr = nb;
   list_alloc_.grow(new_units);
   caps_.list_words = new_units * 4 * kTile;
+  ++struct_ver_;
   return kOK;
 }
 
@@ -516,6 +537,14 @@ int Engine::upload_params(int only) {
       P.rl2f_lo = std::nextafter((float)(P.rl2 * (1.0 - eps)), 0.0f);
       P.rl2f_hi = std::nextafter((float)(P.rl2 * (1.0 + eps)), 3.0e38f);
     }
+    P.skin = h.spec.skin;
+    {
+      // FP32-force validity threshold: each shadow coordinate is within 1/2 unit
+      // of the position, so the integer displacement is compared with
+      // (skin / 2 in units - 4)^2
+      const double hq = 0.5 * h.spec.skin * (4294967296.0 / h.spec.L) - 4.0;
+      P.disp_thr = hq > 0.0 ? hq * hq : 0.0;
+    }
     P.rc2f = (float)P.rc2;
     P.c2f = (float)h.c2;
     P.rlf = (float)h.rl;
@@ -551,6 +580,7 @@ int Engine::set_precision(int mode) {
   if (mode < 0 || mode > 5) { set_error("unknown precision mode"); return kErrArg; }
   if (mode != precision_) {
     precision_ = mode;
+    ++struct_ver_;
     for (SysHost& h : sys_) {
       h.f_valid = false;
       if (h.has_state) h.force_rebuild = true;  // refresh the fixed-point shadow
@@ -755,6 +785,173 @@ int Engine::post_drift(cudaStream_t s) {
   return rebuild(which, s);
 }
 
+// ------------------------------------------------ graph-captured step loop
+
+void Engine::drop_graphs() {
+  for (int p = 0; p < 2; ++p) {
+    if (gexec_[p]) cudaGraphExecDestroy(gexec_[p]);
+    gexec_[p] = nullptr;
+    gver_[p] = -1;
+  }
+}
+
+#define CKG(call)                                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) {                        \
+      set_error(std::string("CUDA graph: ") + cudaGetErrorString(e_)); \
+      return kErrCuda;                              \
+    }                                               \
+  } while (0)
+
+// Loop node (condition set by the second decision of its body) over two steps
+// of opposite buffer parity; after each step the decision kernel and a
+// conditional node holding the rebuild pass of the other parity.
+int Engine::build_graph(cudaGraph_t g, int parity) {
+  const DevArrays a0 = arrays();
+  DevArrays a = a0;
+  a.ctl = d_ctl_;
+  int nused = 0;
+  for (const SysHost& h : sys_) nused += h.used ? 1 : 0;
+  cudaGraphConditionalHandle hw;
+  CKG(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  CKG(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphConditionalHandle hi[2];
+  for (int h = 0; h < 2; ++h) CKG(cudaGraphConditionalHandleCreate(&hi[h], body, 0, cudaGraphCondAssignDefault));
+  CKG(cudaStreamBeginCaptureToGraph(cap_[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = kOK;
+  for (int h = 0; h < 2 && rc == kOK; ++h) {
+    const int c = parity ^ h;
+    // the flags come from the control words (first step of a call, then steady)
+    if (precision_ == 1) launch_step_fp32(a, c, 0.0, 0.0, 0, tuning_, cap_[0]);
+    else launch_step_fp64(a, c, 0.0, 0.0, 0, tuning_, precision_ >= 2 ? precision_ - 1 : 0, cap_[0]);
+    launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, d_rebuild_, d_rebuild_ + nsys(), d_reb_count_, hi[h], hw, h,
+                  cap_[0]);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cap_[0], &st, nullptr, &cg, &deps, &ed, &nd);
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi[h];
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&in, cg, deps, ed, nd, &ip);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cap_[0], &in, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cap_[1], ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const int c1 = c ^ 1;
+      launch_cell_count(a, c1, cap_[1]);
+      launch_cell_scan(a, nused, cap_[1]);
+      launch_scatter(a, cap_[1]);
+      launch_cell_sort(a, c1, nused, max_cells_, cap_[1]);
+      launch_gather(a, c1, cap_[1]);
+      launch_copyback(a, c1, cap_[1]);
+      launch_build_list(a, c1, tuning_, cap_[1]);
+      cudaGraph_t t1 = nullptr;
+      e = cudaStreamEndCapture(cap_[1], &t1);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA graph capture: ") + cudaGetErrorString(e));
+      rc = kErrCuda;
+    }
+  }
+  cudaGraph_t t0 = nullptr;
+  const cudaError_t e0 = cudaStreamEndCapture(cap_[0], &t0);
+  if (rc == kOK && e0 != cudaSuccess) {
+    set_error(std::string("CUDA graph capture: ") + cudaGetErrorString(e0));
+    rc = kErrCuda;
+  }
+  if (rc != kOK) {
+    cudaGraph_t t1 = nullptr;
+    cudaStreamEndCapture(cap_[1], &t1);  // in case the inner capture is still open
+    cudaGetLastError();
+  }
+  return rc;
+}
+
+int Engine::capture_graph(int parity) {
+  if (gexec_[parity]) cudaGraphExecDestroy(gexec_[parity]);
+  gexec_[parity] = nullptr;
+  for (cudaStream_t& c : cap_)
+    if (!c) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  int rc = build_graph(g, parity);
+  if (rc == kOK) {
+    const cudaError_t e = cudaGraphInstantiate(&gexec_[parity], g, 0);
+    if (e != cudaSuccess) {
+      set_error(std::string("CUDA graph instantiate: ") + cudaGetErrorString(e));
+      gexec_[parity] = nullptr;
+      rc = kErrCuda;
+    }
+  }
+  cudaGraphDestroy(g);
+  if (rc == kOK) gver_[parity] = struct_ver_;
+  return rc;
+}
+
+// Runs up to nsteps (even) steps as one graph launch; *done = steps taken.
+int Engine::run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s) {
+  *done = 0;
+  if (!gexec_[cur_] || gver_[cur_] != struct_ver_) CKR(capture_graph(cur_));
+  GraphCtl c{};
+  c.flags = first_flags;
+  c.target = (int32_t)nsteps;
+  *h_ctl_ = c;
+  CK(cudaMemcpyAsync(d_ctl_, h_ctl_, sizeof(GraphCtl), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(d_reb_count_, 0, sizeof(int32_t) * nsys(), s));
+  CK(cudaGraphLaunch(gexec_[cur_], s));
+  CK(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h_reb_count_, d_reb_count_, sizeof(int32_t) * nsys(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(SysStatus) * nsys(), cudaMemcpyDeviceToHost, s));
+  CKR(sync_check(s));
+  const GraphCtl r = *h_ctl_;
+  *done = r.done;
+  if (r.done & 1) cur_ ^= 1;
+  n_launch_ += 2 * (int64_t)r.done + 7 * (int64_t)r.passes;
+  n_rebuild_seq_ += r.passes;
+  for (int k = 0; k < nsys(); ++k) {
+    if (h_reb_count_[k] <= 0) continue;
+    sys_[k].rebuilds += h_reb_count_[k];
+    sys_[k].force_rebuild = false;
+    sys_[k].f_valid = false;
+  }
+  if (r.abort == 2) {
+    for (int k = 0; k < nsys(); ++k)
+      if (sys_[k].used && sys_[k].active && h_status_[k].nonfinite) {
+        set_error("non-finite position or velocity in system " + std::to_string(k));
+        return kErrNonfinite;
+      }
+    set_error("non-finite position or velocity");
+    return kErrNonfinite;
+  }
+  if (r.abort == 1) {
+    // a list overflowed in the last rebuild pass: grow it and rebuild (counted once)
+    std::vector<int> which;
+    for (int k = 0; k < nsys(); ++k)
+      if (sys_[k].used && sys_[k].active && h_status_[k].overflow > 0) {
+        which.push_back(k);
+        sys_[k].rebuilds -= 1;
+      }
+    CKR(rebuild(which, s));
+  }
+  return kOK;
+}
+
 int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) {
   if (nsteps < 0) { set_error("nsteps < 0"); return kErrArg; }
   if ((int)dt.size() != nsys()) { set_error("one dt per system required"); return kErrArg; }
@@ -767,7 +964,17 @@ int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) 
   CKR(upload_params());
   CKR(ensure_lists(s));
   CKR(ensure_forces(s));
-  for (int64_t it = 0; it < nsteps; ++it) {
+  int64_t it = 0;
+  if (graph_ && !timing_) {
+    while (nsteps - it >= 2) {
+      const int first = it == 0 ? (kStepUseStoredF | kStepDrift | kStepKickB) : (kStepKickA | kStepKickB | kStepDrift);
+      int64_t done = 0;
+      const int rc = run_graph(std::min<int64_t>(nsteps - it, 1 << 30) & ~int64_t(1), first, &done, s);
+      it += done;
+      if (rc != kOK) return rc;
+    }
+  }
+  for (; it < nsteps; ++it) {
     if (it == 0) CKR(launch_step(0.0, 0.5, kStepUseStoredF | kStepDrift, s));
     else CKR(launch_step(0.5, 0.5, kStepDrift, s));
     cur_ ^= 1;

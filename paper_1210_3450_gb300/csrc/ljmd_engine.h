@@ -129,7 +129,8 @@ class Engine {
 
   int set_active(int k, bool on);
   // Launch shapes: key 0 = step-kernel threads per block (64/128/256), 1 = FP32
-  // partner groups per iteration (1/2), 2 = list-build threads per block.
+  // partner groups per iteration (1/2), 2 = list-build threads per block, 3 =
+  // list-build variant, 4 = FP32 load hints, 5 = graph-captured step loop (0/1).
   int set_tuning(int key, int value);
   int get_tuning(int key) const;
   // Per-kernel-class device times (CUDA events on the launching stream).
@@ -156,6 +157,16 @@ class Engine {
   int ensure_forces(cudaStream_t s);
   int launch_step(double ka, double kb, int flags, cudaStream_t s);
   int post_drift(cudaStream_t s);
+  // Graph-captured step loop (tuning key 5): a CUDA graph whose loop node runs
+  // two steps per iteration, each followed by the device-side list-validity
+  // decision and a conditional node holding the rebuild pass. The host reads
+  // the control words once per graph launch instead of after every step; a
+  // list overflow or a non-finite value stops the loop (the host grows the list
+  // and resumes, or reports the error), so results equal the host-driven loop's.
+  int capture_graph(int parity);
+  int build_graph(cudaGraph_t g, int parity);
+  void drop_graphs();
+  int run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s);
   int sync_check(cudaStream_t s);
   DevArrays arrays() const;
   enum TimedKind { kTStep = 0, kTList = 1, kTBin = 2 };
@@ -172,6 +183,15 @@ class Engine {
   int64_t t_count_[3] = {0, 0, 0};
   int64_t n_launch_ = 0;
   int64_t n_rebuild_seq_ = 0;
+  bool graph_ = true;
+  int64_t struct_ver_ = 0;  // bumped whenever captured launches would change
+  cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
+  int64_t gver_[2] = {-1, -1};
+  cudaStream_t cap_[2] = {nullptr, nullptr};
+  GraphCtl* d_ctl_ = nullptr;
+  GraphCtl* h_ctl_ = nullptr;
+  int32_t* d_reb_count_ = nullptr;
+  int32_t* h_reb_count_ = nullptr;
 
   std::vector<SysHost> sys_;
   int precision_ = 0;

@@ -17,6 +17,8 @@
 // particle, list membership, wrap into the box, displacement) use explicitly
 // rounded FP64 intrinsics (__dadd_rn, __dmul_rn, ...), so the compiler cannot fuse
 // them into FMAs.
+#include <algorithm>
+
 #include "ljmd_dev.cuh"
 #include "ljmd_math.cuh"
 
@@ -117,49 +119,53 @@ __global__ void k_cell_count(DevArrays a, int cur) {
   a.cell[t.s] = c;
 }
 
-// Exclusive scan of the cell counts of one system per block; the counts are
-// then reset to serve as fill counters of the scatter.
+// Exclusive scan of the cell counts of one rebuilding system per block (blocks
+// stride over the rebuilding systems); the counts are then reset to serve as
+// fill counters of the scatter.
 __global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
-  if ((int)blockIdx.x >= nreb) return;
-  const int sys = a.rebuild_ids[blockIdx.x];
-  const SysParams P = a.params[sys];
-  if (!P.active || !a.rebuild[sys]) return;
+  if (a.ctl) nreb = a.ctl->nreb;  // graph-captured loop: the count is decided on the device
   __shared__ int wsum[32];
   __shared__ int total_s;
-  const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  int carry = 0;
-  for (int64_t base = 0; base < ncell; base += 1024) {
-    const int64_t c = base + tid;
-    const int val = c < ncell ? a.ccount[P.c_off + c] : 0;
-    int incl = val;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-      int ws = wsum[lane];
-      int wi = ws;
+  for (int r = blockIdx.x; r < nreb; r += gridDim.x) {
+    const int sys = a.rebuild_ids[r];
+    const SysParams& P = a.params[sys];
+    if (!P.active || !a.rebuild[sys]) continue;  // uniform over the block
+    const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+    const int64_t c_off = P.c_off;
+    int carry = 0;
+    for (int64_t base = 0; base < ncell; base += 1024) {
+      const int64_t c = base + tid;
+      const int val = c < ncell ? a.ccount[c_off + c] : 0;
+      int incl = val;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, wi, o);
-        if (lane >= o) wi += y;
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
       }
-      wsum[lane] = wi - ws;
-      if (lane == 31) total_s = wi;
+      if (lane == 31) wsum[w] = incl;
+      __syncthreads();
+      if (w == 0) {
+        int ws = wsum[lane];
+        int wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, wi, o);
+          if (lane >= o) wi += y;
+        }
+        wsum[lane] = wi - ws;
+        if (lane == 31) total_s = wi;
+      }
+      __syncthreads();
+      if (c < ncell) {
+        a.cstart[c_off + c] = carry + wsum[w] + incl - val;
+        a.ccount[c_off + c] = 0;
+      }
+      carry += total_s;
+      __syncthreads();
     }
-    __syncthreads();
-    if (c < ncell) {
-      a.cstart[P.c_off + c] = carry + wsum[w] + incl - val;
-      a.ccount[P.c_off + c] = 0;
-    }
-    carry += total_s;
-    __syncthreads();
+    if (tid == 0) a.cstart[c_off + ncell] = carry;
   }
-  if (tid == 0) a.cstart[P.c_off + ncell] = carry;
 }
 
 __global__ void k_scatter(DevArrays a) {
@@ -178,33 +184,38 @@ __global__ void k_scatter(DevArrays a) {
 // Order the particles of each cell by x, ties by caller index (deterministic).
 // A row of neighbouring cells along x is then sorted by x as a whole, which lets
 // the list build restrict each row to the window |x_j - x_i| < rl.
-// Insertion sort: cells hold tens of particles.
-__global__ void k_cell_sort(DevArrays a, int cur) {
-  const int sys = a.rebuild_ids[blockIdx.y];
-  const SysParams P = a.params[sys];
-  if (!P.active || !a.rebuild[sys] || P.nc == 1) return;
-  const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
-  a.ccount[P.c_off + c] = 0;  // ready for the next binning
-  int32_t* pm = a.perm + P.p_off;
-  const int32_t* id = a.id + P.p_off;
-  const double4_32a* xs = a.x[cur] + P.p_off;
-  // keys: x >= 0 (wrapped), so its bit pattern orders like the value
-  for (int k = lo + 1; k < hi; ++k) {
-    const int32_t pk = pm[k];
-    const long long kx = __double_as_longlong(xs[pk].x);
-    const int32_t kid = id[pk];
-    int m = k - 1;
-    while (m >= lo) {
-      const int32_t pmm = pm[m];
-      const long long mx = __double_as_longlong(xs[pmm].x);
-      if (mx < kx || (mx == kx && id[pmm] < kid)) break;
-      pm[m + 1] = pmm;
-      --m;
+// Insertion sort: cells hold tens of particles. Blocks stride over the
+// rebuilding systems (y) and their cells (x).
+__global__ void k_cell_sort(DevArrays a, int cur, int nreb) {
+  if (a.ctl) nreb = a.ctl->nreb;
+  for (int r = blockIdx.y; r < nreb; r += gridDim.y) {
+    const int sys = a.rebuild_ids[r];
+    const SysParams& P = a.params[sys];
+    if (!P.active || !a.rebuild[sys] || P.nc == 1) continue;
+    const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+    int32_t* pm = a.perm + P.p_off;
+    const int32_t* id = a.id + P.p_off;
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
+      a.ccount[P.c_off + c] = 0;  // ready for the next binning
+      // keys: x >= 0 (wrapped), so its bit pattern orders like the value
+      for (int k = lo + 1; k < hi; ++k) {
+        const int32_t pk = pm[k];
+        const long long kx = __double_as_longlong(xs[pk].x);
+        const int32_t kid = id[pk];
+        int m = k - 1;
+        while (m >= lo) {
+          const int32_t pmm = pm[m];
+          const long long mx = __double_as_longlong(xs[pmm].x);
+          if (mx < kx || (mx == kx && id[pmm] < kid)) break;
+          pm[m + 1] = pmm;
+          --m;
+        }
+        pm[m + 1] = pk;
+      }
     }
-    pm[m + 1] = pk;
   }
 }
 
@@ -481,7 +492,10 @@ __device__ __forceinline__ void list_done(const DevArrays& a, int sys, int64_t s
   const int wmax = __reduce_max_sync(mask, act ? count : 0);
   if (lane == __ffs(mask) - 1) {
     atomicMax(&a.status[sys].max_count, wmax);
-    if (wmax > kmax) atomicMax(&a.status[sys].overflow, wmax);
+    if (wmax > kmax) {
+      atomicMax(&a.status[sys].overflow, wmax);
+      if (a.ctl) atomicMax(&a.ctl->abort, 1);  // graph-captured loop: stop; the host grows the list
+    }
   }
 }
 
@@ -763,6 +777,10 @@ __device__ __forceinline__ int4 ld_shadow(const int4* p, bool hint) {
 // unrolling). BLOCK and GROUPS are chosen by the autotuner.
 template <int BLOCK, int GROUPS, bool HINT>
 __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, double ka, double kb, int flags) {
+  if (a.ctl) {  // graph-captured loop (uniform over the grid)
+    if (a.ctl->abort) return;
+    flags = a.ctl->flags;
+  }
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
@@ -860,6 +878,10 @@ __device__ __forceinline__ double force_factor(double r2, double c2x8) {
 
 template <int BLOCK, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
+  if (a.ctl) {  // graph-captured loop (uniform over the grid)
+    if (a.ctl->abort) return;
+    flags = a.ctl->flags;
+  }
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P)) return;
@@ -1041,16 +1063,105 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
   k_to_caller<<<(unsigned)((sys_n + 255) / 256), 256, 0, s>>>(a, cur, which, out, sys);
 }
 
+// ------------------------------------------ graph-captured loop (decision)
+
+// The list-validity decision on the device, the same rule as the host's: the
+// FP32-force form compares the squared fixed-point displacement (an exact
+// integer) with a threshold lowered by 4 units, the FP64 forms test
+// 2 sqrt(d2) >= skin. Writes the rebuild flags, the rebuilding systems in
+// ascending order, resets the displacement maxima, counts steps and passes, and
+// sets the conditions of the rebuild node (h_if) and, after the second step of
+// the loop body (last), of the loop node (h_loop). A non-finite position or
+// velocity stops the loop (abort word 2).
+__global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32, int32_t* rebuild,
+                                                 int32_t* rebuild_ids, int32_t* reb_count,
+                                                 cudaGraphConditionalHandle h_if,
+                                                 cudaGraphConditionalHandle h_loop, int last) {
+  GraphCtl* c = a.ctl;
+  if (c->abort) {  // uniform over the block
+    if (threadIdx.x == 0) {
+      cudaGraphSetConditional(h_if, 0);
+      if (last) cudaGraphSetConditional(h_loop, 0);
+    }
+    return;
+  }
+  __shared__ int wsum[32];
+  __shared__ int base_s, bad_s, total_s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { base_s = 0; bad_s = 0; }
+  __syncthreads();
+  for (int k0 = 0; k0 < nsys; k0 += 1024) {
+    const int k = k0 + (int)threadIdx.x;
+    int need = 0;
+    if (k < nsys) {
+      const unsigned long long d2 = a.disp2[k];
+      a.disp2[k] = 0ull;
+      if (a.params[k].active) {
+        if (a.status[k].nonfinite) bad_s = 1;
+        if (fp32) need = (d2 == ~0ull || __ull2double_rn(d2) >= a.params[k].disp_thr) ? 1 : 0;
+        else need = !(2.0 * __dsqrt_rn(__longlong_as_double((long long)d2)) < a.params[k].skin) ? 1 : 0;
+      }
+      rebuild[k] = need;
+    }
+    const unsigned b = __ballot_sync(kFull, need);
+    if (lane == 0) wsum[w] = __popc(b);
+    __syncthreads();
+    if (w == 0) {
+      const int v = wsum[lane];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      wsum[lane] = incl - v;
+      if (lane == 31) total_s = incl;
+    }
+    __syncthreads();
+    if (need) {
+      rebuild_ids[base_s + wsum[w] + __popc(b & ((1u << lane) - 1u))] = k;
+      reb_count[k] += 1;
+      a.status[k].overflow = 0;
+      a.status[k].max_count = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base_s += total_s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int nreb = base_s;
+    c->done += 1;
+    if (bad_s) {
+      c->abort = 2;
+      cudaGraphSetConditional(h_if, 0);
+      if (last) cudaGraphSetConditional(h_loop, 0);
+      return;
+    }
+    c->nreb = nreb;
+    c->passes += nreb > 0 ? 1 : 0;
+    c->flags = kStepKickA | kStepKickB | kStepDrift;
+    cudaGraphSetConditional(h_if, nreb > 0 ? 1u : 0u);
+    if (last) cudaGraphSetConditional(h_loop, c->done < c->target ? 1u : 0u);
+  }
+}
+
+void launch_decide(const DevArrays& a, int nsys, int fp32, int32_t* rebuild, int32_t* rebuild_ids,
+                   int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
+                   int last, cudaStream_t s) {
+  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, rebuild, rebuild_ids, reb_count, h_if, h_loop, last);
+}
+
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
   k_cell_count<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
-  k_cell_scan<<<nreb, 1024, 0, s>>>(a, nreb);
+  k_cell_scan<<<(unsigned)std::min(std::max(nreb, 1), 1024), 1024, 0, s>>>(a, nreb);
 }
 void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<tile_blocks(a), kBlock, 0, s>>>(a); }
 void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, cudaStream_t s) {
-  dim3 g((unsigned)((max_cells + 127) / 128), (unsigned)nreb);
-  k_cell_sort<<<g, 128, 0, s>>>(a, cur);
+  const dim3 g((unsigned)std::min<int64_t>((max_cells + 127) / 128, 8192),
+               (unsigned)std::min(std::max(nreb, 1), 1024));
+  k_cell_sort<<<g, 128, 0, s>>>(a, cur, nreb);
 }
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<tile_blocks(a), kBlock, 0, s>>>(a, cur); }
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
