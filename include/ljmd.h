@@ -84,6 +84,19 @@ MD_API int md_create(double box_L, int64_t N, double rc, double skin, md_ctx** o
  * invalidated. */
 MD_API int md_set_precision(md_ctx* ctx, int mode);
 
+/* List validity rule (Sec. 2.1: the list is checked every step).
+ *   MD_RULE_DISPLACEMENT (default): rebuild when 2 d_max >= skin, d_max the largest
+ *     displacement since the last build (exact FP64; in MD_FP32_FORCE the exact integer
+ *     displacement of the fixed-point shadow against a threshold 4 units lower).
+ *   MD_RULE_DUTC: the velocity bound of the paper's DUTC check: a margin equal to the skin
+ *     after each build shrinks every step by 2 v_max dt (v_max the largest drift speed,
+ *     FP64) and the list is rebuilt when the margin is no longer positive; it bounds the
+ *     displacements from above, so it rebuilds no later than the displacement rule.
+ * Changing the rule rebuilds the lists before the next step. Errors: MD_ERR_ARG. */
+#define MD_RULE_DISPLACEMENT 0
+#define MD_RULE_DUTC 1
+MD_API int md_set_validity_rule(md_ctx* ctx, int rule);
+
 /* Copy positions x (N*3, any real values: wrapped into [0, L) on entry) and velocities
  * v (N*3) from host memory; forces a list rebuild before the next force evaluation. */
 MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v);
@@ -282,6 +295,8 @@ MD_API int md_batch_usage(md_batch* b, int64_t* out8);
 MD_API int md_batch_set_active(md_batch* b, int id, int on);
 
 MD_API int md_batch_set_precision(md_batch* b, int mode);
+/* List validity rule of every system in the batch (MD_RULE_*), as md_set_validity_rule. */
+MD_API int md_batch_set_validity_rule(md_batch* b, int rule);
 
 /* Per-system state transfer, same conventions as md_set_state / md_get_state. */
 MD_API int md_batch_set_state(md_batch* b, int id, const double* x, const double* v);

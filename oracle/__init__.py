@@ -48,6 +48,8 @@ def _load():
             "orc_run": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64]),
             "orc_run_mode": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64,
                                        C.c_int, C.c_int]),
+            "orc_run_rule": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64,
+                                       C.c_int, C.c_int, C.c_int]),
             "orc_pair_force_factor_rcp": (_D, [_D, _D, _D, C.c_int, C.c_int]),
             "orc_subcell_counts": (None, [_I64, _D, C.c_int, _PD, _PI32]),
             "orc_run_nvt": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _D, _D, _PD, _PI64, _PD, _I64]),
@@ -195,9 +197,10 @@ def observables(x, v, box: float, rc: float, skin: float = 0.3, c2=None, c0=None
 
 
 def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
-        trace_every: int = 0, rcp_bits: int = -1, rcp_corr: bool = False) -> dict:
+        trace_every: int = 0, rcp_bits: int = -1, rcp_corr: bool = False, rule: int = 0) -> dict:
     """Velocity-Verlet run; returns dict(x, v, rebuilds, trace). With rcp_bits >= 0 the
-    forces use the approximate-reciprocal factor of Sec. 3.3."""
+    forces use the approximate-reciprocal factor of Sec. 3.3; rule 1 checks the list
+    with the velocity bound (DUTC) instead of the displacements."""
     x = _f64(x, (-1, 3)).copy()
     v = _f64(v, (-1, 3)).copy()
     rebuilds = _I64(0)
@@ -206,8 +209,9 @@ def run(x, v, box: float, rc: float, skin: float, nsteps: int, dt: float,
     if trace_every > 0:
         trace = np.empty(1 + nsteps // trace_every)
         tp = _pd(trace)
-    rc_ = _load().orc_run_mode(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt,
-                               C.byref(rebuilds), tp, trace_every, int(rcp_bits), 1 if rcp_corr else 0)
+    rc_ = _load().orc_run_rule(x.shape[0], box, rc, skin, _pd(x), _pd(v), nsteps, dt,
+                               C.byref(rebuilds), tp, trace_every, int(rcp_bits), 1 if rcp_corr else 0,
+                               int(rule))
     if rc_ != 0:
         raise MemoryError("oracle run failed to allocate")
     return dict(x=x, v=v, rebuilds=rebuilds.value, trace=trace)

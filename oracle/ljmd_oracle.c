@@ -397,20 +397,41 @@ static void forces_mode(const orc_list_state* s, const double* x, int rcp_bits, 
                             rcp_corr, f);
 }
 
-/* As orc_run, with the approximate-reciprocal force factor when rcp_bits >= 0. */
-ORC_API int orc_run_mode(int64_t n, double box, double rc, double skin, double* x, double* v,
+/* As orc_run, with the approximate-reciprocal force factor when rcp_bits >= 0 and the
+ * list validity rule `rule`: 0 displacement (2 d_max >= skin), 1 velocity bound (the DUTC
+ * check of Sec. 2.1: a margin equal to the skin after each build shrinks by
+ * 2 v_max dt per step, v_max the largest speed used in the drift; rebuild when the margin
+ * is no longer positive). */
+ORC_API int orc_run_rule(int64_t n, double box, double rc, double skin, double* x, double* v,
                          int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
-                         int64_t trace_every, int rcp_bits, int rcp_corr);
+                         int64_t trace_every, int rcp_bits, int rcp_corr, int rule);
 
 ORC_API int orc_run(int64_t n, double box, double rc, double skin, double* x, double* v,
                     int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
                     int64_t trace_every) {
-    return orc_run_mode(n, box, rc, skin, x, v, nsteps, dt, rebuilds, trace, trace_every, -1, 0);
+    return orc_run_rule(n, box, rc, skin, x, v, nsteps, dt, rebuilds, trace, trace_every, -1, 0, 0);
 }
 
 ORC_API int orc_run_mode(int64_t n, double box, double rc, double skin, double* x, double* v,
                          int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
                          int64_t trace_every, int rcp_bits, int rcp_corr) {
+    return orc_run_rule(n, box, rc, skin, x, v, nsteps, dt, rebuilds, trace, trace_every, rcp_bits,
+                        rcp_corr, 0);
+}
+
+/* Largest speed |v_i| = sqrt((vx vx + vy vy) + vz vz). */
+static double max_speed(int64_t n, const double* v) {
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s2 = (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1]) + v[3 * i + 2] * v[3 * i + 2];
+        if (s2 > m) m = s2;
+    }
+    return sqrt(m);
+}
+
+ORC_API int orc_run_rule(int64_t n, double box, double rc, double skin, double* x, double* v,
+                         int64_t nsteps, double dt, int64_t* rebuilds, double* trace,
+                         int64_t trace_every, int rcp_bits, int rcp_corr, int rule) {
     orc_list_state s;
     memset(&s, 0, sizeof(s));
     s.n = n;
@@ -436,11 +457,20 @@ ORC_API int orc_run_mode(int64_t n, double box, double rc, double skin, double* 
         orc_observables_list(n, box, rc, s.c2, s.c0, x, v, s.start, s.partners, o);
         trace[ti++] = o[0] + o[2];
     }
+    double margin = skin;
     for (int64_t step = 1; step <= nsteps; ++step) {
         for (int64_t k = 0; k < 3 * n; ++k) v[k] = v[k] + hdt * f[k];
         for (int64_t k = 0; k < 3 * n; ++k) x[k] = wrap1(x[k] + dt * v[k], box);
-        if (2.0 * max_displacement(&s, x) >= skin) {
+        int rebuild_now;
+        if (rule == 1) {
+            margin = margin - (2.0 * max_speed(n, v)) * dt;
+            rebuild_now = !(margin > 0.0);
+        } else {
+            rebuild_now = 2.0 * max_displacement(&s, x) >= skin;
+        }
+        if (rebuild_now) {
             if (list_rebuild(&s, x)) { rc_ = -1; goto done; }
+            margin = skin;
         }
         forces_mode(&s, x, rcp_bits, rcp_corr, f);
         for (int64_t k = 0; k < 3 * n; ++k) v[k] = v[k] + hdt * f[k];

@@ -84,6 +84,12 @@ int md_set_precision(md_ctx* c, int mode) {
   return c->eng.set_precision(mode);
 }
 
+int md_set_validity_rule(md_ctx* c, int rule) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.set_rule(rule);
+}
+
 int md_set_state(md_ctx* c, const double* x, const double* v) {
   int r = check_ctx(c);
   if (r) return r;
@@ -483,6 +489,12 @@ int md_batch_set_precision(md_batch* b, int mode) {
   int r = check_batch(b);
   if (r) return r;
   return b->eng.set_precision(mode);
+}
+
+int md_batch_set_validity_rule(md_batch* b, int rule) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_rule(rule);
 }
 
 int md_batch_set_state(md_batch* b, int id, const double* x, const double* v) {

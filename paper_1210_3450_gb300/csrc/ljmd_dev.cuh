@@ -60,6 +60,7 @@ struct SysParams {
   int32_t t_off;     // first global tile
   int32_t ntiles;    // tiles of this system
   int32_t active;    // 1 if the system takes part in the current launches
+  int32_t rule;      // list validity: 0 displacement (2 d_max >= skin), 1 velocity bound (DUTC)
 };
 
 // Per-system status words written by kernels and read by the host.
@@ -77,6 +78,8 @@ enum StepFlags : int {
   kStepUseStoredF = 4,  // take F from the stored buffer instead of the pair loop
   kStepKickA = 8,       // v += dt/2 F completing the previous step
   kStepKickB = 16,      // v += dt/2 F, first half-kick of the next step
+  kStepVmax = 32,       // report max |v|^2 of the drift velocities (velocity-bound rule) instead of
+                        // the displacement
 };
 
 // Control words of the graph-captured step loop (device-resident; NULL in
@@ -115,7 +118,8 @@ struct DevArrays {
   // systems
   const SysParams* params;
   SysStatus* status;
-  unsigned long long* disp2;  // per system: max squared displacement (double bits)
+  unsigned long long* disp2;  // per system: max squared displacement, or max |v|^2 (double bits)
+  double* margin;             // per system: velocity-bound rule's remaining margin
   const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
   const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
   const int32_t* tile_sys;  // system of each global tile
@@ -145,7 +149,8 @@ void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
 // Device-side list-validity decision of the graph-captured loop (see GraphCtl).
-void launch_decide(const DevArrays& a, int nsys, int fp32, int32_t* rebuild, int32_t* rebuild_ids,
+// reb_count NULL: outside a graph (no step or pass counting, no node conditions).
+void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* rebuild, int32_t* rebuild_ids,
                    int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
                    int last, cudaStream_t s);
 // mode 0: FP64 reciprocal; 1..4: approximate reciprocal of Sec. 3.3 (8 bits,

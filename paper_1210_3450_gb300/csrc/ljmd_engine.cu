@@ -284,7 +284,7 @@ void Engine::free_all() {
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.ccount); dfree(d_.cstart);
-  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_rebuild_); dfree(d_tile_sys_);
+  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_);
   drop_graphs();
@@ -372,6 +372,8 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_params_, ns));
   CKR(dmalloc(&d_status_, ns));
   CKR(dmalloc(&d_disp2_, ns));
+  CKR(dmalloc(&d_margin_, ns));
+  CK(cudaMemset(d_margin_, 0, sizeof(double) * ns));
   CKR(dmalloc(&d_rebuild_, 2 * ns));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
@@ -559,6 +561,7 @@ int Engine::upload_params(int only) {
     P.t_off = h.t_off;
     P.ntiles = h.ntiles;
     P.active = h.active ? 1 : 0;
+    P.rule = rule_;
   }
   CK(cudaMemcpy(d_params_ + k0, ps.data(), sizeof(SysParams) * ps.size(), cudaMemcpyHostToDevice));
   return kOK;
@@ -569,6 +572,7 @@ DevArrays Engine::arrays() const {
   a.params = d_params_;
   a.status = d_status_;
   a.disp2 = d_disp2_;
+  a.margin = d_margin_;
   a.rebuild = d_rebuild_;
   a.rebuild_ids = d_rebuild_ + nsys();
   a.tile_sys = d_tile_sys_;
@@ -585,6 +589,19 @@ int Engine::set_precision(int mode) {
       h.f_valid = false;
       if (h.has_state) h.force_rebuild = true;  // refresh the fixed-point shadow
     }
+  }
+  return kOK;
+}
+
+int Engine::set_rule(int rule) {
+  if (rule != 0 && rule != 1) { set_error("unknown list validity rule"); return kErrArg; }
+  if (rule != rule_) {
+    rule_ = rule;
+    ++struct_ver_;
+    // the margin is only tracked under the velocity bound: start from fresh lists
+    for (SysHost& h : sys_)
+      if (h.has_state) h.force_rebuild = true;
+    CKR(upload_params());
   }
   return kOK;
 }
@@ -720,6 +737,7 @@ int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
   // dt/2 from the system parameters, so they need no FP64 compare or product)
   if (ka != 0.0) flags |= kStepKickA;
   if (kb != 0.0) flags |= kStepKickB;
+  if ((flags & kStepDrift) && rule_ == 1) flags |= kStepVmax;
   tmark_begin(kTStep, s);
   if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
   else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, precision_ >= 2 ? precision_ - 1 : 0, s);
@@ -755,33 +773,32 @@ int Engine::ensure_forces(cudaStream_t s) {
   return kOK;
 }
 
-// After a drift: read the displacement maxima, stop on non-finite values, and
-// rebuild the systems whose list is no longer valid (2 d_max >= skin).
+// After a drift: the list-validity decision (k_decide, the kernel the graph loop
+// uses), read back with the status words; stop on non-finite values and rebuild
+// the systems whose list is no longer valid.
 int Engine::post_drift(cudaStream_t s) {
-  CK(cudaMemcpyAsync(h_disp2_, d_disp2_, sizeof(unsigned long long) * nsys(), cudaMemcpyDeviceToHost, s));
+  DevArrays a = arrays();
+  a.ctl = d_ctl_;
+  launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, rule_ == 1 ? kStepVmax : 0, d_rebuild_, d_rebuild_ + nsys(),
+                nullptr, 0, 0, 0, s);
+  CKL();
+  n_launch_ += 1;
+  CK(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h_rebuild_, d_rebuild_, sizeof(int32_t) * nsys(), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(SysStatus) * nsys(), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemsetAsync(d_disp2_, 0, sizeof(unsigned long long) * nsys(), s));
   CKR(sync_check(s));
-  std::vector<int> which;
-  for (int k = 0; k < nsys(); ++k) {
-    SysHost& h = sys_[k];
-    if (!h.active) continue;
-    if (h_status_[k].nonfinite) {
-      set_error("non-finite position or velocity in system " + std::to_string(k));
-      return kErrNonfinite;
-    }
-    if (precision_ == 1) {
-      // FP32-force form: exact integer check of the fixed-point shadow, with the
-      // threshold lowered by 4 units (each shadow coordinate is within 1/2 unit)
-      const double hq = 0.5 * h.spec.skin * (4294967296.0 / h.spec.L) - 4.0;
-      const double thr = hq > 0.0 ? hq * hq : 0.0;
-      if (h_disp2_[k] == ~0ull || (double)h_disp2_[k] >= thr) which.push_back(k);
-    } else {
-      double d2;
-      std::memcpy(&d2, &h_disp2_[k], sizeof(double));
-      if (!(2.0 * std::sqrt(d2) < h.spec.skin)) which.push_back(k);
-    }
+  if (h_ctl_->abort == 2) {
+    for (int k = 0; k < nsys(); ++k)
+      if (sys_[k].used && sys_[k].active && h_status_[k].nonfinite) {
+        set_error("non-finite position or velocity in system " + std::to_string(k));
+        return kErrNonfinite;
+      }
+    set_error("non-finite position or velocity");
+    return kErrNonfinite;
   }
+  std::vector<int> which;
+  for (int k = 0; k < nsys(); ++k)
+    if (sys_[k].active && h_rebuild_[k]) which.push_back(k);
   return rebuild(which, s);
 }
 
@@ -832,8 +849,8 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
     // the flags come from the control words (first step of a call, then steady)
     if (precision_ == 1) launch_step_fp32(a, c, 0.0, 0.0, 0, tuning_, cap_[0]);
     else launch_step_fp64(a, c, 0.0, 0.0, 0, tuning_, precision_ >= 2 ? precision_ - 1 : 0, cap_[0]);
-    launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, d_rebuild_, d_rebuild_ + nsys(), d_reb_count_, hi[h], hw, h,
-                  cap_[0]);
+    launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, rule_ == 1 ? kStepVmax : 0, d_rebuild_, d_rebuild_ + nsys(),
+                  d_reb_count_, hi[h], hw, h, cap_[0]);
     cudaStreamCaptureStatus st;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -964,10 +981,12 @@ int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) 
   CKR(upload_params());
   CKR(ensure_lists(s));
   CKR(ensure_forces(s));
+  CK(cudaMemsetAsync(d_ctl_, 0, sizeof(GraphCtl), s));
   int64_t it = 0;
   if (graph_ && !timing_) {
     while (nsteps - it >= 2) {
-      const int first = it == 0 ? (kStepUseStoredF | kStepDrift | kStepKickB) : (kStepKickA | kStepKickB | kStepDrift);
+      const int first = (it == 0 ? (kStepUseStoredF | kStepDrift | kStepKickB) : (kStepKickA | kStepKickB | kStepDrift)) |
+                        (rule_ == 1 ? kStepVmax : 0);
       int64_t done = 0;
       const int rc = run_graph(std::min<int64_t>(nsteps - it, 1 << 30) & ~int64_t(1), first, &done, s);
       it += done;

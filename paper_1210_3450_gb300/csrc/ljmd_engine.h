@@ -95,6 +95,9 @@ class Engine {
   void arena_usage(int64_t* out8) const;
 
   int set_precision(int mode);
+  // List validity rule: 0 displacement (2 d_max >= skin), 1 velocity bound (DUTC).
+  int set_rule(int rule);
+  int rule() const { return rule_; }
   int precision() const { return precision_; }
   int nsys() const { return (int)sys_.size(); }
   const SysHost& sys(int k) const { return sys_[k]; }
@@ -195,6 +198,7 @@ class Engine {
 
   std::vector<SysHost> sys_;
   int precision_ = 0;
+  int rule_ = 0;
   int cur_ = 0;
   ArenaCaps caps_{0, 0, 0, 0};
   bool list_growable_ = false;  // exact-size arenas grow their list storage on demand
@@ -207,6 +211,7 @@ class Engine {
   SysParams* d_params_ = nullptr;
   SysStatus* d_status_ = nullptr;
   unsigned long long* d_disp2_ = nullptr;
+  double* d_margin_ = nullptr;
   int32_t* d_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;

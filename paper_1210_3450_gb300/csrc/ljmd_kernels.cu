@@ -164,7 +164,10 @@ __global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
       carry += total_s;
       __syncthreads();
     }
-    if (tid == 0) a.cstart[c_off + ncell] = carry;
+    if (tid == 0) {
+      a.cstart[c_off + ncell] = carry;
+      a.margin[sys] = P.skin;  // velocity-bound rule: a fresh list has the whole skin
+    }
   }
 }
 
@@ -703,14 +706,20 @@ __device__ __forceinline__ unsigned long long integrate(const DevArrays& a, cons
     a.status[t.sys].nonfinite = 1;
     return ~0ull;
   }
+  // velocity-bound rule: |v|^2 of the drift velocity, (vx vx + vy vy) + vz vz unfused
+  const unsigned long long v2b =
+      (unsigned long long)__double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)),
+                                                         __dmul_rn(v.z, v.z)));
   if (kFP32) {
     // check in fixed point: exact integer squared displacement of the shadow
     const int4 q = fixed4(xn, P.qscale);
     a.xq[cur ^ 1][t.s] = q;
     const int4 r = a.xqref[t.s];
     const long long ex = wrapped_diff(q.x, r.x), ey = wrapped_diff(q.y, r.y), ez = wrapped_diff(q.z, r.z);
+    if (flags & kStepVmax) return v2b;
     return (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey) + (unsigned long long)(ez * ez);
   }
+  if (flags & kStepVmax) return v2b;
   // exact FP64 check, the same operations as the reference
   const double4_32a r = a.xref[t.s];
   const double ex = __dsub_rn(xn.x, r.x), ey = __dsub_rn(xn.y, r.y), ez = __dsub_rn(xn.z, r.z);
@@ -1065,21 +1074,26 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
 
 // ------------------------------------------ graph-captured loop (decision)
 
-// The list-validity decision on the device, the same rule as the host's: the
-// FP32-force form compares the squared fixed-point displacement (an exact
-// integer) with a threshold lowered by 4 units, the FP64 forms test
-// 2 sqrt(d2) >= skin. Writes the rebuild flags, the rebuilding systems in
-// ascending order, resets the displacement maxima, counts steps and passes, and
-// sets the conditions of the rebuild node (h_if) and, after the second step of
-// the loop body (last), of the loop node (h_loop). A non-finite position or
-// velocity stops the loop (abort word 2).
-__global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32, int32_t* rebuild,
+// The list-validity decision after a drift (Sec. 2.1: the list is checked every
+// step), for the graph-captured loop and for the host-driven one alike.
+// Displacement rule: the FP32-force form compares the squared fixed-point
+// displacement (an exact integer) with a threshold lowered by 4 units, the FP64
+// forms test 2 sqrt(d2) >= skin. Velocity-bound rule (the DUTC check): the
+// margin, the whole skin after a rebuild, shrinks by 2 v_max dt each step, and
+// the list is rebuilt when it is no longer positive. Writes the rebuild flags
+// and the rebuilding systems in ascending order, resets the per-step maxima, and
+// in a graph (reb_count set) counts steps, passes and rebuilds and sets the
+// conditions of the rebuild node (h_if) and, after the second step of the loop
+// body (last), of the loop node (h_loop). A non-finite position or velocity
+// stops the loop (abort word 2).
+__global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32, int vflag, int32_t* rebuild,
                                                  int32_t* rebuild_ids, int32_t* reb_count,
                                                  cudaGraphConditionalHandle h_if,
                                                  cudaGraphConditionalHandle h_loop, int last) {
   GraphCtl* c = a.ctl;
+  const bool graph = reb_count != nullptr;
   if (c->abort) {  // uniform over the block
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && graph) {
       cudaGraphSetConditional(h_if, 0);
       if (last) cudaGraphSetConditional(h_loop, 0);
     }
@@ -1096,10 +1110,22 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     if (k < nsys) {
       const unsigned long long d2 = a.disp2[k];
       a.disp2[k] = 0ull;
-      if (a.params[k].active) {
+      const SysParams& P = a.params[k];
+      if (P.active) {
         if (a.status[k].nonfinite) bad_s = 1;
-        if (fp32) need = (d2 == ~0ull || __ull2double_rn(d2) >= a.params[k].disp_thr) ? 1 : 0;
-        else need = !(2.0 * __dsqrt_rn(__longlong_as_double((long long)d2)) < a.params[k].skin) ? 1 : 0;
+        if (P.rule == 1) {
+          // velocity bound (DUTC): the margin shrinks by 2 v_max dt per step; a
+          // rebuild restores it (k_cell_scan)
+          const double m =
+              __dsub_rn(a.margin[k],
+                        __dmul_rn(__dmul_rn(2.0, __dsqrt_rn(__longlong_as_double((long long)d2))), P.dt));
+          a.margin[k] = m;
+          need = (d2 == ~0ull || !(m > 0.0)) ? 1 : 0;
+        } else if (fp32) {
+          need = (d2 == ~0ull || __ull2double_rn(d2) >= P.disp_thr) ? 1 : 0;
+        } else {
+          need = !(2.0 * __dsqrt_rn(__longlong_as_double((long long)d2)) < P.skin) ? 1 : 0;
+        }
       }
       rebuild[k] = need;
     }
@@ -1120,7 +1146,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     __syncthreads();
     if (need) {
       rebuild_ids[base_s + wsum[w] + __popc(b & ((1u << lane) - 1u))] = k;
-      reb_count[k] += 1;
+      if (graph) reb_count[k] += 1;
       a.status[k].overflow = 0;
       a.status[k].max_count = 0;
     }
@@ -1133,22 +1159,26 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     c->done += 1;
     if (bad_s) {
       c->abort = 2;
-      cudaGraphSetConditional(h_if, 0);
-      if (last) cudaGraphSetConditional(h_loop, 0);
+      if (graph) {
+        cudaGraphSetConditional(h_if, 0);
+        if (last) cudaGraphSetConditional(h_loop, 0);
+      }
       return;
     }
     c->nreb = nreb;
     c->passes += nreb > 0 ? 1 : 0;
-    c->flags = kStepKickA | kStepKickB | kStepDrift;
-    cudaGraphSetConditional(h_if, nreb > 0 ? 1u : 0u);
-    if (last) cudaGraphSetConditional(h_loop, c->done < c->target ? 1u : 0u);
+    c->flags = kStepKickA | kStepKickB | kStepDrift | vflag;
+    if (graph) {
+      cudaGraphSetConditional(h_if, nreb > 0 ? 1u : 0u);
+      if (last) cudaGraphSetConditional(h_loop, c->done < c->target ? 1u : 0u);
+    }
   }
 }
 
-void launch_decide(const DevArrays& a, int nsys, int fp32, int32_t* rebuild, int32_t* rebuild_ids,
+void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* rebuild, int32_t* rebuild_ids,
                    int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
                    int last, cudaStream_t s) {
-  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, rebuild, rebuild_ids, reb_count, h_if, h_loop, last);
+  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_count, h_if, h_loop, last);
 }
 
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {

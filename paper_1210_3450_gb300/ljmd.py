@@ -29,6 +29,8 @@ MD_FP64_RCP8_CORR = 3
 MD_FP64_RCP23 = 4
 MD_FP64_RCP23_CORR = 5
 MD_MAX_N = (1 << 26) - 1
+MD_RULE_DISPLACEMENT = 0
+MD_RULE_DUTC = 1
 MD_TUNE_STEP_BLOCK = 0
 MD_TUNE_STEP_GROUPS = 1
 MD_TUNE_LIST_BLOCK = 2
@@ -56,6 +58,7 @@ _PI32 = C.POINTER(C.c_int32)
 SIGNATURES = {
     "md_create": (C.c_int, [C.c_double, C.c_int64, C.c_double, C.c_double, C.POINTER(_P)]),
     "md_set_precision": (C.c_int, [_P, C.c_int]),
+    "md_set_validity_rule": (C.c_int, [_P, C.c_int]),
     "md_set_state": (C.c_int, [_P, _PD, _PD]),
     "md_set_state_dev": (C.c_int, [_P, _P, _P, _P]),
     "md_get_state": (C.c_int, [_P, _PD, _PD]),
@@ -94,6 +97,7 @@ SIGNATURES = {
     "md_batch_usage": (C.c_int, [_P, _PI64]),
     "md_batch_set_active": (C.c_int, [_P, C.c_int, C.c_int]),
     "md_batch_set_precision": (C.c_int, [_P, C.c_int]),
+    "md_batch_set_validity_rule": (C.c_int, [_P, C.c_int]),
     "md_batch_set_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
     "md_batch_set_state_dev": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "md_batch_get_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
@@ -199,6 +203,9 @@ class LJSystem:
     # C ABI calls
     def set_precision(self, mode: int):
         _check(_lib.md_set_precision(self._h, int(mode)))
+
+    def set_validity_rule(self, rule: int):
+        _check(_lib.md_set_validity_rule(self._h, int(rule)))
 
     def set_state(self, x, v):
         x = _host3(x, self.n)
@@ -408,6 +415,9 @@ class LJBatch:
 
     def set_precision(self, mode: int):
         _check(_lib.md_batch_set_precision(self._h, int(mode)))
+
+    def set_validity_rule(self, rule: int):
+        _check(_lib.md_batch_set_validity_rule(self._h, int(rule)))
 
     def set_state(self, sid: int, x, v):
         n = self._n[sid]

@@ -529,3 +529,47 @@ def test_nvt_holds_the_temperature(oracle):
         xs, vs, z, e = r["x"], r["v"], r["zeta"], r["eta"]
         temps.append(float((vs ** 2).sum() / (3 * (len(xs) - 1))))
     assert abs(np.mean(temps) - 0.9) < 0.05 * 0.9
+
+
+# ------------------------------------------- list validity: velocity bound (DUTC)
+
+@pytest.mark.parametrize("u", [0.7, 1.3, 2.9])
+def test_dutc_free_particle_closed_form(oracle, u):
+    """One particle in free flight (its partner out of range, at rest): both rules
+    rebuild every k = ceil(skin / (2 u dt)) steps, k the first step count whose
+    displacement (and accumulated velocity bound) reaches skin / 2."""
+    x = np.array([[5.0, 5.0, 5.0], [15.0, 15.0, 15.0]])
+    v = np.array([[u, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    skin, dt, nsteps = 0.3, 0.005, 300
+    k = int(np.ceil(skin / (2.0 * u * dt)))
+    assert skin / (2.0 * u * dt) != k                # no tie at the threshold
+    for rule in (0, 1):
+        r = oracle.run(x, v, 20.0, 2.5, skin, nsteps, dt, rule=rule)
+        assert r["rebuilds"] == 1 + nsteps // k
+
+
+def test_dutc_bounds_displacement_on_a_vibrating_dimer(oracle):
+    """A bound dimer oscillates by less than skin / 2, so the displacement rule
+    never rebuilds after the first build; the velocity bound keeps accumulating
+    v_max dt and rebuilds periodically. The list (one pair) is the same either
+    way, so the trajectories are identical."""
+    x = np.array([[5.0, 5.0, 5.0], [6.2, 5.0, 5.0]])
+    v = np.zeros((2, 3))
+    a = oracle.run(x, v, 12.0, 2.5, 0.3, 2000, 0.005, rule=0)
+    b = oracle.run(x, v, 12.0, 2.5, 0.3, 2000, 0.005, rule=1)
+    assert a["rebuilds"] == 1
+    assert b["rebuilds"] > 5
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["v"], b["v"])
+
+
+def test_dutc_never_rebuilds_later(oracle):
+    """The velocity bound is an upper bound of the displacement, so on a fluid it
+    rebuilds at least as often, and the two runs agree closely (the lists hold
+    the same pairs; only the partner order, hence the rounding, may differ)."""
+    x, box = li.perturbed_fcc(1372, 0.8442, 0.05, 31)
+    v = li.maxwell_boltzmann(1372, 1.2, 32)
+    a = oracle.run(x, v, box, 2.5, 0.3, 150, 0.005, rule=0)
+    b = oracle.run(x, v, box, 2.5, 0.3, 150, 0.005, rule=1)
+    assert b["rebuilds"] >= a["rebuilds"] > 5
+    assert np.abs(a["x"] - b["x"]).max() < 1e-9
