@@ -97,6 +97,21 @@ MD_API int md_set_precision(md_ctx* ctx, int mode);
 #define MD_RULE_DUTC 1
 MD_API int md_set_validity_rule(md_ctx* ctx, int rule);
 
+/* Pair-list form.
+ *   MD_LIST_FULL (default): every particle lists all its partners and sums its own
+ *     force (no Newton's third law), as the paper's FX10 kernel (Sec. 3.3).
+ *   MD_LIST_HALF: each pair is listed once (Sec. 2.1: pairs i < j; here in the list of the
+ *     pair's lower slot in cell order) and its force is added to both particles, the
+ *     partner's share by FP64 atomic additions; the step takes two launches (forces,
+ *     then the update). The order of the atomic additions varies between runs, so results
+ *     vary in the last bits. md_get_list then returns each pair once; md_pair_stats counts
+ *     each pair once. The warp-cooperative list build (MD_TUNE_LIST_VARIANT 4) builds full
+ *     lists only and gives way to variant 0. Changing the form rebuilds the lists.
+ * Errors: MD_ERR_ARG. */
+#define MD_LIST_FULL 0
+#define MD_LIST_HALF 1
+MD_API int md_set_pair_list(md_ctx* ctx, int kind);
+
 /* Copy positions x (N*3, any real values: wrapped into [0, L) on entry) and velocities
  * v (N*3) from host memory; forces a list rebuild before the next force evaluation. */
 MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v);
@@ -297,6 +312,8 @@ MD_API int md_batch_set_active(md_batch* b, int id, int on);
 MD_API int md_batch_set_precision(md_batch* b, int mode);
 /* List validity rule of every system in the batch (MD_RULE_*), as md_set_validity_rule. */
 MD_API int md_batch_set_validity_rule(md_batch* b, int rule);
+/* Pair-list form of every system in the batch (MD_LIST_*), as md_set_pair_list. */
+MD_API int md_batch_set_pair_list(md_batch* b, int kind);
 
 /* Per-system state transfer, same conventions as md_set_state / md_get_state. */
 MD_API int md_batch_set_state(md_batch* b, int id, const double* x, const double* v);

@@ -45,6 +45,7 @@ def _load():
             "orc_force_on": (None, [_I64, _D, _D, _D, _PD, _I64, _PD]),
             "orc_forces_brute": (None, [_I64, _D, _D, _D, _PD, _PD]),
             "orc_observables_list": (None, [_I64, _D, _D, _D, _D, _PD, _PD, _PI64, _PI32, _PD]),
+            "orc_forces_half": (None, [_I64, _D, _D, _D, _PD, _PI64, _PI32, _PD]),
             "orc_run": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64]),
             "orc_run_mode": (C.c_int, [_I64, _D, _D, _D, _PD, _PD, _I64, _D, _PI64, _PD, _I64,
                                        C.c_int, C.c_int]),
@@ -136,6 +137,18 @@ def forces_list(x, box: float, rc: float, c2: float, start, partners) -> np.ndar
     partners = np.ascontiguousarray(partners, dtype=np.int32)
     _load().orc_forces_list(x.shape[0], box, rc, c2, _pd(x), start.ctypes.data_as(_PI64),
                             partners.ctypes.data_as(_PI32), _pd(f))
+    return f
+
+
+def forces_half(x, box: float, rc: float, skin: float = 0.3) -> np.ndarray:
+    """Forces with Newton's third law: each pair i < j of the list once, +g r on i
+    and -g r on j."""
+    x = _f64(x, (-1, 3))
+    start, partners = build_list(x, box, rc + skin)
+    c2, _ = lj_coeffs(rc)
+    f = np.empty_like(x)
+    _load().orc_forces_half(x.shape[0], box, rc, c2, _pd(x), np.ascontiguousarray(start).ctypes.data_as(_PI64),
+                            np.ascontiguousarray(partners, dtype=np.int32).ctypes.data_as(_PI32), _pd(f))
     return f
 
 

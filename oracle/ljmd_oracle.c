@@ -266,6 +266,30 @@ ORC_API void orc_forces_list(int64_t n, double box, double rc, double c2, const 
     }
 }
 
+/* Forces with Newton's third law (Sec. 2.1: each pair once, i < j, the key particle's
+ * sum gets +g r and the partner's -g r), taking from the full list only the partners
+ * j > i, in list order. */
+ORC_API void orc_forces_half(int64_t n, double box, double rc, double c2, const double* x,
+                             const int64_t* start, const int32_t* partners, double* f) {
+    double rc2 = rc * rc;
+    for (int64_t k = 0; k < 3 * n; ++k) f[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = start[i]; k < start[i + 1]; ++k) {
+            int64_t j = partners[k];
+            if (j <= i) continue;
+            double dx, dy, dz;
+            double r2 = dist2(x, i, j, box, &dx, &dy, &dz);
+            double g = orc_pair_force_factor(r2, rc2, c2);
+            f[3 * i + 0] += g * dx;
+            f[3 * i + 1] += g * dy;
+            f[3 * i + 2] += g * dz;
+            f[3 * j + 0] -= g * dx;
+            f[3 * j + 1] -= g * dy;
+            f[3 * j + 2] -= g * dz;
+        }
+    }
+}
+
 /* Forces over the list with the approximate-reciprocal force factor. */
 ORC_API void orc_forces_list_rcp(int64_t n, double box, double rc, double c2, const double* x,
                                  const int64_t* start, const int32_t* partners, int bits, int corr,

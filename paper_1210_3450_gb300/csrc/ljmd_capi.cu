@@ -90,6 +90,12 @@ int md_set_validity_rule(md_ctx* c, int rule) {
   return c->eng.set_rule(rule);
 }
 
+int md_set_pair_list(md_ctx* c, int kind) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.set_list_kind(kind);
+}
+
 int md_set_state(md_ctx* c, const double* x, const double* v) {
   int r = check_ctx(c);
   if (r) return r;
@@ -495,6 +501,12 @@ int md_batch_set_validity_rule(md_batch* b, int rule) {
   int r = check_batch(b);
   if (r) return r;
   return b->eng.set_rule(rule);
+}
+
+int md_batch_set_pair_list(md_batch* b, int kind) {
+  int r = check_batch(b);
+  if (r) return r;
+  return b->eng.set_list_kind(kind);
 }
 
 int md_batch_set_state(md_batch* b, int id, const double* x, const double* v) {

@@ -61,6 +61,7 @@ struct SysParams {
   int32_t ntiles;    // tiles of this system
   int32_t active;    // 1 if the system takes part in the current launches
   int32_t rule;      // list validity: 0 displacement (2 d_max >= skin), 1 velocity bound (DUTC)
+  int32_t half;      // 1: half list (each pair once, in its lower slot's list; Newton's third law)
 };
 
 // Per-system status words written by kernels and read by the host.
@@ -99,7 +100,8 @@ struct DevArrays {
   double4_32a* v;         // velocities
   double4_32a* xref;      // positions at the last list build (FP64 form's check)
   int4* xqref;        // shadow positions at the last list build (FP32-force form's check)
-  double4_32a* f;         // stored forces (double)
+  double4_32a* f;         // stored forces (double); half list: the own-list sums of the step
+  double4_32a* facc;      // half list: forces added by the partners' threads (atomics), zeroed on use
   int4* xq[2];        // fixed-point shadow positions (uint32 per axis, wraps at L)
   int32_t* id;        // caller index of each slot, -1 for padding
   int32_t* cell;      // cell of each slot (valid after binning)
@@ -157,6 +159,9 @@ void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* r
 // 8 bits corrected, 23 bits, 23 bits corrected)
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       int mode, cudaStream_t s);
+// Half list (Newton's third law): pair forces with atomic scatter to the partners,
+// then the velocity-Verlet update from own + scattered sums (two launches).
+void launch_step_half(const DevArrays& a, int cur, int flags, const Tuning& tu, int precision, cudaStream_t s);
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s);
 // select: per-system flags (NULL = every active system)

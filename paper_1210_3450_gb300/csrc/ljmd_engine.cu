@@ -281,7 +281,7 @@ int footprint(const SysSpec& s, SysFootprint* f, SysHost* h) {
 
 void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
-  dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
+  dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.ccount); dfree(d_.cstart);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
@@ -348,6 +348,8 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.xref, P));
   CKR(dmalloc(&d_.xqref, P));
   CKR(dmalloc(&d_.f, P));
+  CKR(dmalloc(&d_.facc, P));
+  CK(cudaMemset(d_.facc, 0, sizeof(double4_32a) * P));
   CKR(dmalloc(&d_.id, P));
   CKR(dmalloc(&d_.cell, P));
   CKR(dmalloc(&d_.ncnt, P));
@@ -562,6 +564,7 @@ int Engine::upload_params(int only) {
     P.ntiles = h.ntiles;
     P.active = h.active ? 1 : 0;
     P.rule = rule_;
+    P.half = half_ ? 1 : 0;
   }
   CK(cudaMemcpy(d_params_ + k0, ps.data(), sizeof(SysParams) * ps.size(), cudaMemcpyHostToDevice));
   return kOK;
@@ -601,6 +604,20 @@ int Engine::set_rule(int rule) {
     // the margin is only tracked under the velocity bound: start from fresh lists
     for (SysHost& h : sys_)
       if (h.has_state) h.force_rebuild = true;
+    CKR(upload_params());
+  }
+  return kOK;
+}
+
+int Engine::set_list_kind(int kind) {
+  if (kind != 0 && kind != 1) { set_error("unknown pair-list kind"); return kErrArg; }
+  if ((kind == 1) != half_) {
+    half_ = kind == 1;
+    ++struct_ver_;
+    for (SysHost& h : sys_) {
+      h.f_valid = false;
+      if (h.has_state) h.force_rebuild = true;
+    }
     CKR(upload_params());
   }
   return kOK;
@@ -666,7 +683,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     launch_copyback(a, cur_, s);
     tmark_end(s);
     tmark_begin(kTList, s);
-    launch_build_list(a, cur_, tuning_, s);
+    launch_build_list(a, cur_, list_tuning(), s);
     tmark_end(s);
     CKL();
     n_launch_ += 7;
@@ -739,11 +756,12 @@ int Engine::launch_step(double ka, double kb, int flags, cudaStream_t s) {
   if (kb != 0.0) flags |= kStepKickB;
   if ((flags & kStepDrift) && rule_ == 1) flags |= kStepVmax;
   tmark_begin(kTStep, s);
-  if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
+  if (half_) launch_step_half(a, cur_, flags, tuning_, precision_, s);
+  else if (precision_ == 1) launch_step_fp32(a, cur_, ka, kb, flags, tuning_, s);
   else launch_step_fp64(a, cur_, ka, kb, flags, tuning_, precision_ >= 2 ? precision_ - 1 : 0, s);
   tmark_end(s);
   CKL();
-  n_launch_ += 1;
+  n_launch_ += half_ ? 2 : 1;
   return kOK;
 }
 
@@ -847,7 +865,8 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
   for (int h = 0; h < 2 && rc == kOK; ++h) {
     const int c = parity ^ h;
     // the flags come from the control words (first step of a call, then steady)
-    if (precision_ == 1) launch_step_fp32(a, c, 0.0, 0.0, 0, tuning_, cap_[0]);
+    if (half_) launch_step_half(a, c, 0, tuning_, precision_, cap_[0]);
+    else if (precision_ == 1) launch_step_fp32(a, c, 0.0, 0.0, 0, tuning_, cap_[0]);
     else launch_step_fp64(a, c, 0.0, 0.0, 0, tuning_, precision_ >= 2 ? precision_ - 1 : 0, cap_[0]);
     launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, rule_ == 1 ? kStepVmax : 0, d_rebuild_, d_rebuild_ + nsys(),
                   d_reb_count_, hi[h], hw, h, cap_[0]);
@@ -876,7 +895,7 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
       launch_cell_sort(a, c1, nused, max_cells_, cap_[1]);
       launch_gather(a, c1, cap_[1]);
       launch_copyback(a, c1, cap_[1]);
-      launch_build_list(a, c1, tuning_, cap_[1]);
+      launch_build_list(a, c1, list_tuning(), cap_[1]);
       cudaGraph_t t1 = nullptr;
       e = cudaStreamEndCapture(cap_[1], &t1);
     }
@@ -939,7 +958,7 @@ int Engine::run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream
   const GraphCtl r = *h_ctl_;
   *done = r.done;
   if (r.done & 1) cur_ ^= 1;
-  n_launch_ += 2 * (int64_t)r.done + 7 * (int64_t)r.passes;
+  n_launch_ += (half_ ? 3 : 2) * (int64_t)r.done + 7 * (int64_t)r.passes;
   n_rebuild_seq_ += r.passes;
   for (int k = 0; k < nsys(); ++k) {
     if (h_reb_count_[k] <= 0) continue;

@@ -98,6 +98,8 @@ class Engine {
   // List validity rule: 0 displacement (2 d_max >= skin), 1 velocity bound (DUTC).
   int set_rule(int rule);
   int rule() const { return rule_; }
+  // Pair list: 0 full (default), 1 half with Newton's third law (atomic scatter).
+  int set_list_kind(int kind);
   int precision() const { return precision_; }
   int nsys() const { return (int)sys_.size(); }
   const SysHost& sys(int k) const { return sys_[k]; }
@@ -172,6 +174,12 @@ class Engine {
   int run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s);
   int sync_check(cudaStream_t s);
   DevArrays arrays() const;
+  // Tuning of the list build (the warp-cooperative variant builds full lists only).
+  Tuning list_tuning() const {
+    Tuning t = tuning_;
+    if (half_ && t.list_variant == 4) t.list_variant = 0;
+    return t;
+  }
   enum TimedKind { kTStep = 0, kTList = 1, kTBin = 2 };
   void tmark_begin(int kind, cudaStream_t s);
   void tmark_end(cudaStream_t s);
@@ -199,6 +207,7 @@ class Engine {
   std::vector<SysHost> sys_;
   int precision_ = 0;
   int rule_ = 0;
+  bool half_ = false;
   int cur_ = 0;
   ArenaCaps caps_{0, 0, 0, 0};
   bool list_growable_ = false;  // exact-size arenas grow their list storage on demand

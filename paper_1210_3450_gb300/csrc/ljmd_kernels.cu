@@ -284,6 +284,7 @@ struct ListCtx {
   int li;                 // the particle's slot in the system
   int count;
   int kmax;
+  bool half;              // half list: only partners in higher slots
   // Append e when p holds (a predicated store).
   __device__ __forceinline__ void push_if(bool p, uint32_t e) {
     if (p && count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
@@ -362,6 +363,11 @@ __device__ __forceinline__ void sweep_range(const PreTest<PRE>& T, ListCtx& o, i
     unsigned m = (r0 < T.hi2 ? 1u : 0u) | (r1 < T.hi2 ? 2u : 0u) | (r2 < T.hi2 ? 4u : 0u) | (r3 < T.hi2 ? 8u : 0u);
     m &= (hi - j) >= 4 ? 15u : ((1u << (hi - j)) - 1u);
     if ((unsigned)(o.li - j) < 4u) m &= ~(1u << (o.li - j));  // not the particle itself
+    if (o.half) {  // half list: keep candidates j + k > li
+      const int d = o.li - j;
+      if (d >= 3) m = 0u;
+      else if (d >= 0) m &= ~((2u << d) - 1u);
+    }
     if (m) {
       const unsigned in = m & ((r0 < T.lo2 ? 1u : 0u) | (r1 < T.lo2 ? 2u : 0u) | (r2 < T.lo2 ? 4u : 0u) |
                                (r3 < T.lo2 ? 8u : 0u));
@@ -389,7 +395,7 @@ __device__ __forceinline__ void sweep_all(ListCtx& o, const int4* __restrict__ q
     const float ax = (float)wrapped_diff(qj.x, qi.x);
     const float ay = (float)wrapped_diff(qj.y, qi.y);
     const float az = (float)wrapped_diff(qj.z, qi.z);
-    if (j != o.li && fmaf(az, az, fmaf(ay, ay, ax * ax)) < hi2) o.exact(j, 0xffu);
+    if (j != o.li && (!o.half || j > o.li) && fmaf(az, az, fmaf(ay, ay, ax * ax)) < hi2) o.exact(j, 0xffu);
   }
 }
 
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
   if (li >= n) return;
   const int64_t p_off = Pp->p_off;
   const int kmax = Pp->kmax;
-  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax};
+  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
   if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
   else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
   list_done(a, sys, p_off + li, o.count, kmax, true, __activemask(), lane);
@@ -537,7 +543,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
 // in candidate order. Candidates outside a lane's own three cells are farther
 // than the cell side >= rl, so they fail its test; every cell of the union
 // appears once, with one image, because a group spans at most nc - 2 cells
-// (wider runs of a row are split into several groups).
+// (wider runs of a row are split into several groups). Full lists only.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArrays a, int cur) {
   __shared__ float4 sbuf[BLOCK];
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArra
   const unsigned actm = __ballot_sync(kFull, act);
   const int64_t p_off = Pp->p_off;
   const int kmax = Pp->kmax;
-  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax};
+  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, false};
   const int nc = Pp->nc;
   if (nc == 1) {
     if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
@@ -933,10 +939,128 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
   warp_max_disp(a, t.sys, d2b, flags);
 }
 
+// ------------------------------------ half list with Newton's third law
+
+// The paper's form before its FX10 kernel (Sec. 2.1 lists each pair once, i < j;
+// Sec. 3.3 drops Newton's third law for the SIMD kernel): each pair is listed once,
+// in the list of its lower slot; the thread of that slot adds the pair force to
+// its own sum and scatters the opposite force to the partner with FP64 atomics.
+// The own sum goes to f, the scattered sums to facc; k_integrate_half adds them.
+// The order of the atomic additions varies, so results vary in the last bits.
+template <int BLOCK, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_force_half_fp64(DevArrays a, int cur, int flags) {
+  if (a.ctl) {  // graph-captured loop (uniform over the grid)
+    if (a.ctl->abort) return;
+    flags = a.ctl->flags;
+  }
+  if (flags & kStepUseStoredF) return;
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !t.act) return;
+  const int lane = threadIdx.x & 31;
+  const double4_32a xi = a.x[cur][t.s];
+  const int cnt = a.ncnt[t.s];
+  const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+  const double4_32a* xs = a.x[cur] + P.p_off;
+  double4_32a* fa = a.facc + P.p_off;
+  const long long rc2b = __double_as_longlong(P.rc2);
+  const double c2x8 = 8.0 * P.c2, L = P.L;
+  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
+    const uint32_t j = e & kIdxMask;
+    const double4_32a xj = xs[j];
+    double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+    const unsigned code = e >> kIdxBits;
+    if (code) {
+      dx = apply_image(dx, code & 3u, L);
+      dy = apply_image(dy, (code >> 2) & 3u, L);
+      dz = apply_image(dz, (code >> 4) & 3u, L);
+    }
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    if (__double_as_longlong(r2) < rc2b) {
+      const double g = force_factor<MODE>(r2, c2x8);
+      const double fx = g * dx, fy = g * dy, fz = g * dz;
+      Fx += fx;
+      Fy += fy;
+      Fz += fz;
+      atomicAdd(&fa[j].x, -fx);
+      atomicAdd(&fa[j].y, -fy);
+      atomicAdd(&fa[j].z, -fz);
+    }
+  }
+  a.f[t.s] = make_double4_32a(Fx, Fy, Fz, 0.0);
+}
+
+// FP32-force form of the same: pair forces in FP32 from the fixed-point
+// separation, own sum in FP32, scattered sums in FP64.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_force_half_fp32(DevArrays a, int cur, int flags) {
+  if (a.ctl) {
+    if (a.ctl->abort) return;
+    flags = a.ctl->flags;
+  }
+  if (flags & kStepUseStoredF) return;
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !t.act) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = a.ncnt[t.s];
+  const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+  const int4* qs = a.xq[cur] + P.p_off;
+  const int4 qi = a.xq[cur][t.s];
+  double4_32a* fa = a.facc + P.p_off;
+  const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (int k = 0; k < cnt; ++k) {
+    const uint32_t j = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3)) & kIdxMask;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    pair_fp32(qi, qs[j], true, qu, rc2, c2x8, px, py, pz);
+    fx += px;
+    fy += py;
+    fz += pz;
+    if (px != 0.f || py != 0.f || pz != 0.f) {
+      atomicAdd(&fa[j].x, -f2d_bits(px));
+      atomicAdd(&fa[j].y, -f2d_bits(py));
+      atomicAdd(&fa[j].z, -f2d_bits(pz));
+    }
+  }
+  a.f[t.s] = make_double4_32a(f2d_bits(fx), f2d_bits(fy), f2d_bits(fz), 0.0);
+}
+
+// Velocity-Verlet update of the half-list form: F = own sum + scattered sums
+// (the latter reset for the next step), or the stored F.
+template <bool kFP32>
+__global__ void __launch_bounds__(kBlock) k_integrate_half(DevArrays a, int cur, int flags) {
+  if (a.ctl) {
+    if (a.ctl->abort) return;
+    flags = a.ctl->flags;
+  }
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P)) return;
+  double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+  double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+  unsigned long long d2b = 0ull;
+  if (t.act) {
+    xi = a.x[cur][t.s];
+    const double4_32a f = a.f[t.s];
+    Fx = f.x; Fy = f.y; Fz = f.z;
+    if (!(flags & kStepUseStoredF)) {
+      const double4_32a g = a.facc[t.s];
+      Fx += g.x; Fy += g.y; Fz += g.z;
+      a.facc[t.s] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+    d2b = integrate<kFP32>(a, P, t, cur, xi, Fx, Fy, Fz, 0.0, 0.0, flags);
+  }
+  warp_max_disp(a, t.sys, d2b, flags);
+}
+
 // ------------------------------------------------- observables (FP64 sums)
 
 // Per particle: 1/2 sum_j V(r) and 1/2 sum_j -r V'(r) over listed partners with
-// r < rc (the full list counts each pair twice), and 1/2 |v|^2; each tile sums
+// r < rc (the full list counts each pair twice; a half list once, without the
+// 1/2), and 1/2 |v|^2; each tile sums
 // its 32 values in a fixed shuffle order into tile_obs[3 t ...].
 __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs,
                                                       const int32_t* __restrict__ select) {
@@ -966,8 +1090,10 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
         w += 48.0 * ir6 * ir6 - 24.0 * ir6 - 8.0 * P.c2 * r2;
       }
     }
-    pe *= 0.5;
-    w *= 0.5;
+    if (!P.half) {  // the full list counts each pair twice
+      pe *= 0.5;
+      w *= 0.5;
+    }
   }
   if (t.act) {
     const double4_32a v = a.v[t.s];
@@ -1247,6 +1373,35 @@ void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int fla
     default: launch_step_fp64_m<0>(a, cur, ka, kb, flags, tu.step_block, s); break;
   }
 }
+template <int MODE>
+static void launch_force_half_fp64_m(const DevArrays& a, int cur, int flags, int block, cudaStream_t s) {
+  switch (block) {
+    case 64: k_force_half_fp64<64, MODE><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, flags); break;
+    case 256: k_force_half_fp64<256, MODE><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, flags); break;
+    default: k_force_half_fp64<128, MODE><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, flags); break;
+  }
+}
+
+void launch_step_half(const DevArrays& a, int cur, int flags, const Tuning& tu, int precision, cudaStream_t s) {
+  if (precision == 1) {
+    switch (tu.step_block) {
+      case 64: k_force_half_fp32<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, flags); break;
+      case 256: k_force_half_fp32<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, flags); break;
+      default: k_force_half_fp32<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, flags); break;
+    }
+    k_integrate_half<true><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, flags);
+    return;
+  }
+  switch (precision) {
+    case 2: launch_force_half_fp64_m<1>(a, cur, flags, tu.step_block, s); break;
+    case 3: launch_force_half_fp64_m<2>(a, cur, flags, tu.step_block, s); break;
+    case 4: launch_force_half_fp64_m<3>(a, cur, flags, tu.step_block, s); break;
+    case 5: launch_force_half_fp64_m<4>(a, cur, flags, tu.step_block, s); break;
+    default: launch_force_half_fp64_m<0>(a, cur, flags, tu.step_block, s); break;
+  }
+  k_integrate_half<false><<<tile_blocks(a), kBlock, 0, s>>>(a, cur, flags);
+}
+
 void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       cudaStream_t s) {
   const int b = tu.step_block, g = tu.step_groups;

@@ -31,6 +31,8 @@ MD_FP64_RCP23_CORR = 5
 MD_MAX_N = (1 << 26) - 1
 MD_RULE_DISPLACEMENT = 0
 MD_RULE_DUTC = 1
+MD_LIST_FULL = 0
+MD_LIST_HALF = 1
 MD_TUNE_STEP_BLOCK = 0
 MD_TUNE_STEP_GROUPS = 1
 MD_TUNE_LIST_BLOCK = 2
@@ -59,6 +61,7 @@ SIGNATURES = {
     "md_create": (C.c_int, [C.c_double, C.c_int64, C.c_double, C.c_double, C.POINTER(_P)]),
     "md_set_precision": (C.c_int, [_P, C.c_int]),
     "md_set_validity_rule": (C.c_int, [_P, C.c_int]),
+    "md_set_pair_list": (C.c_int, [_P, C.c_int]),
     "md_set_state": (C.c_int, [_P, _PD, _PD]),
     "md_set_state_dev": (C.c_int, [_P, _P, _P, _P]),
     "md_get_state": (C.c_int, [_P, _PD, _PD]),
@@ -98,6 +101,7 @@ SIGNATURES = {
     "md_batch_set_active": (C.c_int, [_P, C.c_int, C.c_int]),
     "md_batch_set_precision": (C.c_int, [_P, C.c_int]),
     "md_batch_set_validity_rule": (C.c_int, [_P, C.c_int]),
+    "md_batch_set_pair_list": (C.c_int, [_P, C.c_int]),
     "md_batch_set_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
     "md_batch_set_state_dev": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "md_batch_get_state": (C.c_int, [_P, C.c_int, _PD, _PD]),
@@ -206,6 +210,9 @@ class LJSystem:
 
     def set_validity_rule(self, rule: int):
         _check(_lib.md_set_validity_rule(self._h, int(rule)))
+
+    def set_pair_list(self, kind: int):
+        _check(_lib.md_set_pair_list(self._h, int(kind)))
 
     def set_state(self, x, v):
         x = _host3(x, self.n)
@@ -418,6 +425,9 @@ class LJBatch:
 
     def set_validity_rule(self, rule: int):
         _check(_lib.md_batch_set_validity_rule(self._h, int(rule)))
+
+    def set_pair_list(self, kind: int):
+        _check(_lib.md_batch_set_pair_list(self._h, int(kind)))
 
     def set_state(self, sid: int, x, v):
         n = self._n[sid]

@@ -35,6 +35,7 @@ def main(argv=None):
     p.add_argument("--step-hint", type=int, default=None)
     p.add_argument("--list-variant", type=int, default=None)
     p.add_argument("--autotune", action="store_true")
+    p.add_argument("--half", action="store_true", help="half pair list with Newton's third law")
     a = p.parse_args(argv)
     import lj_inputs as li
     from paper_1210_3450_gb300 import build
@@ -52,6 +53,9 @@ def main(argv=None):
                if val is not None}
         if tun:
             s.set_tuning(**tun)
+        if a.half:
+            from paper_1210_3450_gb300.ljmd import MD_LIST_HALF
+            s.set_pair_list(MD_LIST_HALF)
         s.set_state(x, v)
         tuned = None
         if a.autotune:

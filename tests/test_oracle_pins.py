@@ -573,3 +573,25 @@ def test_dutc_never_rebuilds_later(oracle):
     b = oracle.run(x, v, box, 2.5, 0.3, 150, 0.005, rule=1)
     assert b["rebuilds"] >= a["rebuilds"] > 5
     assert np.abs(a["x"] - b["x"]).max() < 1e-9
+
+
+# ------------------------------------------- half list with Newton's third law
+
+def test_forces_half_equal_full_list(oracle):
+    """Each pair once, +g r on i and -g r on j: the same forces as the full list
+    up to the order of the additions, and a zero total force."""
+    x, box = li.perturbed_fcc(2048, 0.8442, 0.1, 41)
+    fh = oracle.forces_half(x, box, 2.5)
+    ff = oracle.forces(x, box, 2.5)
+    rms = np.sqrt((ff ** 2).sum(1).mean())
+    assert np.abs(fh - ff).max() / rms < 1e-13
+    assert np.abs(fh.sum(0)).max() / rms < 1e-12
+
+
+def test_forces_half_dimer_exact(oracle):
+    """One pair: both sides are the same product, so the forces are equal and
+    opposite bit for bit, and equal to the full list's."""
+    x = np.array([[5.0, 5.0, 5.0], [6.1, 5.3, 4.8]])
+    fh = oracle.forces_half(x, 10.0, 2.5)
+    np.testing.assert_array_equal(fh[0], -fh[1])
+    np.testing.assert_array_equal(fh, oracle.forces(x, 10.0, 2.5))
