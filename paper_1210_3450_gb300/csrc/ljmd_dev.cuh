@@ -114,7 +114,8 @@ struct DevArrays {
   float4* xf;         // positions as float at the last list build (list pre-test; 4 spare entries)
   int32_t* idtmp;
   int32_t* celltmp;
-  int32_t* perm;      // new slot -> old slot
+  int32_t* perm;      // scattered position -> old slot (cell order, arbitrary within a cell)
+  int32_t* perm2;     // new slot -> old slot (within a cell by x, then caller index)
   int32_t* ccount;    // particles per cell (then fill counters)
   int32_t* cstart;    // first slot of each cell (relative to the system), ncell + 1 per system
   // systems
@@ -146,7 +147,7 @@ struct Tuning {
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
 void launch_scatter(const DevArrays& a, cudaStream_t s);
-void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, cudaStream_t s);
+void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s);
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);

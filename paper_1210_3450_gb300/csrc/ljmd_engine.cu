@@ -283,7 +283,7 @@ void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
-  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.ccount); dfree(d_.cstart);
+  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_);
@@ -362,6 +362,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.idtmp, P));
   CKR(dmalloc(&d_.celltmp, P));
   CKR(dmalloc(&d_.perm, P));
+  CKR(dmalloc(&d_.perm2, P));
   CKR(dmalloc(&d_.ccount, caps_.cells));
   CKR(dmalloc(&d_.cstart, caps_.cells));
   CK(cudaMemset(d_.v, 0, sizeof(double4_32a) * P));
@@ -664,11 +665,9 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
   if (which.empty()) return kOK;
   for (int attempt = 0; attempt < 4; ++attempt) {
     for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = 0;
-    int64_t reb_cells = 1;
     for (size_t q = 0; q < which.size(); ++q) {
       h_rebuild_[which[q]] = 1;
       h_rebuild_[nsys() + q] = which[q];
-      reb_cells = std::max(reb_cells, sys_[which[q]].ncell);
     }
     const int nreb = (int)which.size();
     CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (nsys() + nreb), cudaMemcpyHostToDevice, s));
@@ -678,7 +677,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     launch_cell_count(a, cur_, s);
     launch_cell_scan(a, nreb, s);
     launch_scatter(a, s);
-    launch_cell_sort(a, cur_, nreb, reb_cells, s);
+    launch_cell_rank(a, cur_, s);
     launch_gather(a, cur_, s);
     launch_copyback(a, cur_, s);
     tmark_end(s);
@@ -892,7 +891,7 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
       launch_cell_count(a, c1, cap_[1]);
       launch_cell_scan(a, nused, cap_[1]);
       launch_scatter(a, cap_[1]);
-      launch_cell_sort(a, c1, nused, max_cells_, cap_[1]);
+      launch_cell_rank(a, c1, cap_[1]);
       launch_gather(a, c1, cap_[1]);
       launch_copyback(a, c1, cap_[1]);
       launch_build_list(a, c1, list_tuning(), cap_[1]);

@@ -120,8 +120,11 @@ __global__ void k_cell_count(DevArrays a, int cur) {
 }
 
 // Exclusive scan of the cell counts of one rebuilding system per block (blocks
-// stride over the rebuilding systems); the counts are then reset to serve as
-// fill counters of the scatter.
+// stride over the rebuilding systems). Each of the 32 warps owns a contiguous
+// segment of cells read 32 at a time (coalesced): pass 1 sums the segment, one
+// warp scans the 32 segment sums, pass 2 scans the segment with its offset and
+// writes the starts; the counts are reset to serve as fill counters of the
+// scatter.
 __global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
   if (a.ctl) nreb = a.ctl->nreb;  // graph-captured loop: the count is decided on the device
   __shared__ int wsum[32];
@@ -132,42 +135,49 @@ __global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
     const SysParams& P = a.params[sys];
     if (!P.active || !a.rebuild[sys]) continue;  // uniform over the block
     const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
-    const int64_t c_off = P.c_off;
-    int carry = 0;
-    for (int64_t base = 0; base < ncell; base += 1024) {
-      const int64_t c = base + tid;
-      const int val = c < ncell ? a.ccount[c_off + c] : 0;
-      int incl = val;
+    int32_t* cnt = a.ccount + P.c_off;
+    int32_t* cst = a.cstart + P.c_off;
+    const int64_t seg = (ncell + 1023) / 1024 * 32;  // a multiple of 32
+    const int64_t s0 = min(ncell, (int64_t)w * seg), s1 = min(ncell, s0 + seg);
+    int part = 0;
+#pragma unroll 4
+    for (int64_t c = s0 + lane; c < s1; c += 32) part += cnt[c];
+    const int wtot = __reduce_add_sync(kFull, part);
+    if (lane == 0) wsum[w] = wtot;
+    __syncthreads();
+    if (w == 0) {
+      const int ws = wsum[lane];
+      int wi = ws;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - ws;
+      if (lane == 31) total_s = wi;
+    }
+    __syncthreads();
+    int carry = wsum[w];
+    for (int64_t b = s0; b < s1; b += 32) {
+      const int64_t c = b + lane;
+      const int v = c < s1 ? cnt[c] : 0;
+      int incl = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += y;
       }
-      if (lane == 31) wsum[w] = incl;
-      __syncthreads();
-      if (w == 0) {
-        int ws = wsum[lane];
-        int wi = ws;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, wi, o);
-          if (lane >= o) wi += y;
-        }
-        wsum[lane] = wi - ws;
-        if (lane == 31) total_s = wi;
+      if (c < s1) {
+        cst[c] = carry + incl - v;
+        cnt[c] = 0;
       }
-      __syncthreads();
-      if (c < ncell) {
-        a.cstart[c_off + c] = carry + wsum[w] + incl - val;
-        a.ccount[c_off + c] = 0;
-      }
-      carry += total_s;
-      __syncthreads();
+      carry += __shfl_sync(kFull, incl, 31);
     }
     if (tid == 0) {
-      a.cstart[c_off + ncell] = carry;
+      cst[ncell] = total_s;
       a.margin[sys] = P.skin;  // velocity-bound rule: a fresh list has the whole skin
     }
+    __syncthreads();  // wsum and total_s are reused by the next system
   }
 }
 
@@ -186,47 +196,43 @@ __global__ void k_scatter(DevArrays a) {
 
 // Order the particles of each cell by x, ties by caller index (deterministic).
 // A row of neighbouring cells along x is then sorted by x as a whole, which lets
-// the list build restrict each row to the window |x_j - x_i| < rl.
-// Insertion sort: cells hold tens of particles. Blocks stride over the
-// rebuilding systems (y) and their cells (x).
-__global__ void k_cell_sort(DevArrays a, int cur, int nreb) {
-  if (a.ctl) nreb = a.ctl->nreb;
-  for (int r = blockIdx.y; r < nreb; r += gridDim.y) {
-    const int sys = a.rebuild_ids[r];
-    const SysParams& P = a.params[sys];
-    if (!P.active || !a.rebuild[sys] || P.nc == 1) continue;
-    const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
-    int32_t* pm = a.perm + P.p_off;
-    const int32_t* id = a.id + P.p_off;
-    const double4_32a* xs = a.x[cur] + P.p_off;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
-      const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
-      a.ccount[P.c_off + c] = 0;  // ready for the next binning
-      // keys: x >= 0 (wrapped), so its bit pattern orders like the value
-      for (int k = lo + 1; k < hi; ++k) {
-        const int32_t pk = pm[k];
-        const long long kx = __double_as_longlong(xs[pk].x);
-        const int32_t kid = id[pk];
-        int m = k - 1;
-        while (m >= lo) {
-          const int32_t pmm = pm[m];
-          const long long mx = __double_as_longlong(xs[pmm].x);
-          if (mx < kx || (mx == kx && id[pmm] < kid)) break;
-          pm[m + 1] = pmm;
-          --m;
-        }
-        pm[m + 1] = pk;
-      }
-    }
+// the list build restrict each row to the window |x_j - x_i| < rl. One thread per
+// particle: its place in the cell is the number of the cell's particles with a
+// smaller key (x bits, then caller index), counted over the scattered members.
+// The first member of each cell resets the cell's fill counter.
+__global__ void k_cell_rank(DevArrays a, int cur) {
+  TileCtx t;
+  SysParams P;
+  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
+  const int32_t* pm = a.perm + P.p_off;
+  const int p = t.local;  // position in the scattered order
+  const int i = pm[p];    // the particle's slot before the rebuild
+  if (P.nc == 1) {
+    a.perm2[t.s] = i;
+    return;
   }
+  const int c = a.cell[P.p_off + i];
+  const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
+  if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
+  const double4_32a* xs = a.x[cur] + P.p_off;
+  const int32_t* id = a.id + P.p_off;
+  // keys: x >= 0 (wrapped), so its bit pattern orders like the value
+  const long long ki = __double_as_longlong(xs[i].x);
+  const int32_t idi = id[i];
+  int rank = 0;
+  for (int q = lo; q < hi; ++q) {
+    const int j = pm[q];
+    const long long kj = __double_as_longlong(xs[j].x);
+    rank += (kj < ki || (kj == ki && id[j] < idi)) ? 1 : 0;
+  }
+  a.perm2[P.p_off + lo + rank] = i;
 }
 
 __global__ void k_gather(DevArrays a, int cur) {
   TileCtx t;
   SysParams P;
   if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  const int64_t old = P.p_off + a.perm[t.s];
+  const int64_t old = P.p_off + a.perm2[t.s];
   a.xtmp[t.s] = a.x[cur][old];
   a.vtmp[t.s] = a.v[old];
   a.idtmp[t.s] = a.id[old];
@@ -1314,10 +1320,8 @@ void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
   k_cell_scan<<<(unsigned)std::min(std::max(nreb, 1), 1024), 1024, 0, s>>>(a, nreb);
 }
 void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<tile_blocks(a), kBlock, 0, s>>>(a); }
-void launch_cell_sort(const DevArrays& a, int cur, int nreb, int64_t max_cells, cudaStream_t s) {
-  const dim3 g((unsigned)std::min<int64_t>((max_cells + 127) / 128, 8192),
-               (unsigned)std::min(std::max(nreb, 1), 1024));
-  k_cell_sort<<<g, 128, 0, s>>>(a, cur, nreb);
+void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s) {
+  k_cell_rank<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<tile_blocks(a), kBlock, 0, s>>>(a, cur); }
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
