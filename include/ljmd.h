@@ -6,12 +6,15 @@
  * Molecular Dynamics Simulation of Multibubble Nuclei" (arXiv:1210.3450):
  *     V(r) = 4 [ r^-12 - r^-6 + c2 r^2 + c0 ]   for r < rc, 0 otherwise,
  * with c2 = 6 rc^-14 - 3 rc^-8 and c0 = 4 rc^-6 - 7 rc^-12 so that V(rc) = V'(rc) = 0
- * (reduced units: sigma = epsilon = k_B = m = 1). Forces come from a full Verlet
- * pair list (radius rl = rc + skin, Sec. 2.1 "bookkeeping method") built from a cell
- * grid (Sec. 2.1 "grid algorithm"), without Newton's third law (Sec. 3.3). The time
- * integrator is the second-order symplectic velocity-Verlet scheme (Sec. 3.2, 4.1).
- * The list is rebuilt when twice the largest displacement since the last build
- * reaches the skin (the list-validity check of Sec. 2.1).
+ * (reduced units: sigma = epsilon = k_B = m = 1). Forces come from a Verlet pair
+ * list (radius rl = rc + skin, Sec. 2.1 "bookkeeping method") built from a cell grid
+ * (Sec. 2.1 "grid algorithm"): by default a full list without Newton's third law
+ * (Sec. 3.3), optionally a half list with it (md_set_pair_list). The time integrator
+ * is the second-order symplectic velocity-Verlet scheme (Sec. 3.2, 4.1), optionally
+ * with a Nose-Hoover thermostat (md_step_nvt). By default the list is rebuilt when
+ * twice the largest displacement since the last build reaches the skin (the
+ * list-validity check of Sec. 2.1); md_set_validity_rule selects the velocity bound
+ * instead.
  *
  * Conventions for every call:
  *   - Return value 0 (MD_OK) on success, a negative MD_ERR_* code on failure;
