@@ -92,7 +92,8 @@ struct GraphCtl {
   int32_t done;    // steps taken
   int32_t target;  // steps to take
   int32_t passes;  // rebuild passes taken
-  int32_t pad_[2];
+  int32_t next_tile;  // list build's work counter
+  int32_t pad_;
 };
 
 struct DevArrays {
@@ -125,6 +126,9 @@ struct DevArrays {
   double* margin;             // per system: velocity-bound rule's remaining margin
   const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
   const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
+  const int32_t* reb_pref;    // exclusive prefix of the rebuilding systems' tile counts (nreb + 1)
+  int32_t nreb;               // rebuilding systems (host-driven passes; the graph reads ctl->nreb)
+  int32_t* tile_next;         // work counter of the list build (reset before each build)
   const int32_t* tile_sys;  // system of each global tile
   int32_t ntiles;
   GraphCtl* ctl;            // graph-captured loop: step flags, rebuild count, abort word
@@ -154,8 +158,8 @@ void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream
 // Device-side list-validity decision of the graph-captured loop (see GraphCtl).
 // reb_count NULL: outside a graph (no step or pass counting, no node conditions).
 void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* rebuild, int32_t* rebuild_ids,
-                   int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
-                   int last, cudaStream_t s);
+                   int32_t* reb_pref, int32_t* reb_count, cudaGraphConditionalHandle h_if,
+                   cudaGraphConditionalHandle h_loop, int last, cudaStream_t s);
 // mode 0: FP64 reciprocal; 1..4: approximate reciprocal of Sec. 3.3 (8 bits,
 // 8 bits corrected, 23 bits, 23 bits corrected)
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,

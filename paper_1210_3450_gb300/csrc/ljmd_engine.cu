@@ -377,7 +377,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_disp2_, ns));
   CKR(dmalloc(&d_margin_, ns));
   CK(cudaMemset(d_margin_, 0, sizeof(double) * ns));
-  CKR(dmalloc(&d_rebuild_, 2 * ns));
+  CKR(dmalloc(&d_rebuild_, 3 * ns + 1));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
   CKR(dmalloc(&d_pairs_, 2 * ns));
@@ -387,7 +387,7 @@ int Engine::alloc_arrays() {
   CK(cudaMemset(d_tile_sys_, 0xff, sizeof(int32_t) * T));
   CK(cudaMallocHost((void**)&h_status_, sizeof(SysStatus) * ns));
   CK(cudaMallocHost((void**)&h_disp2_, sizeof(unsigned long long) * ns));
-  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * 2 * ns));
+  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * (3 * ns + 1)));
   CK(cudaMallocHost((void**)&h_obs_, sizeof(double) * 3 * ns));
   CKR(dmalloc(&d_ctl_, 1));
   CKR(dmalloc(&d_reb_count_, ns));
@@ -579,6 +579,9 @@ DevArrays Engine::arrays() const {
   a.margin = d_margin_;
   a.rebuild = d_rebuild_;
   a.rebuild_ids = d_rebuild_ + nsys();
+  a.reb_pref = d_rebuild_ + 2 * nsys();
+  a.nreb = 0;
+  a.tile_next = &d_ctl_->next_tile;
   a.tile_sys = d_tile_sys_;
   a.ntiles = ntiles_;
   return a;
@@ -665,14 +668,21 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
   if (which.empty()) return kOK;
   for (int attempt = 0; attempt < 4; ++attempt) {
     for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = 0;
+    int32_t* pref = h_rebuild_ + 2 * nsys();
+    int32_t tiles = 0;
     for (size_t q = 0; q < which.size(); ++q) {
       h_rebuild_[which[q]] = 1;
       h_rebuild_[nsys() + q] = which[q];
+      pref[q] = tiles;
+      tiles += sys_[which[q]].ntiles;
     }
     const int nreb = (int)which.size();
-    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (nsys() + nreb), cudaMemcpyHostToDevice, s));
+    pref[nreb] = tiles;
+    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (3 * nsys() + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(d_status_, 0, sizeof(SysStatus) * nsys(), s));
-    const DevArrays a = arrays();
+    CK(cudaMemsetAsync(&d_ctl_->next_tile, 0, sizeof(int32_t), s));
+    DevArrays a = arrays();
+    a.nreb = nreb;
     tmark_begin(kTBin, s);
     launch_cell_count(a, cur_, s);
     launch_cell_scan(a, nreb, s);
@@ -797,7 +807,7 @@ int Engine::post_drift(cudaStream_t s) {
   DevArrays a = arrays();
   a.ctl = d_ctl_;
   launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, rule_ == 1 ? kStepVmax : 0, d_rebuild_, d_rebuild_ + nsys(),
-                nullptr, 0, 0, 0, s);
+                d_rebuild_ + 2 * nsys(), nullptr, 0, 0, 0, s);
   CKL();
   n_launch_ += 1;
   CK(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
@@ -868,7 +878,7 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
     else if (precision_ == 1) launch_step_fp32(a, c, 0.0, 0.0, 0, tuning_, cap_[0]);
     else launch_step_fp64(a, c, 0.0, 0.0, 0, tuning_, precision_ >= 2 ? precision_ - 1 : 0, cap_[0]);
     launch_decide(a, nsys(), precision_ == 1 ? 1 : 0, rule_ == 1 ? kStepVmax : 0, d_rebuild_, d_rebuild_ + nsys(),
-                  d_reb_count_, hi[h], hw, h, cap_[0]);
+                  d_rebuild_ + 2 * nsys(), d_reb_count_, hi[h], hw, h, cap_[0]);
     cudaStreamCaptureStatus st;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;

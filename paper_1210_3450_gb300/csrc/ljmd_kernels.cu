@@ -53,6 +53,41 @@ __device__ __forceinline__ bool tile_ctx(const DevArrays& a, TileCtx& t, SysPara
   return true;
 }
 
+// Tile w of the rebuilding systems (in rebuild order; reb_pref holds the prefix of
+// their tile counts): false if its system is inactive.
+__device__ __forceinline__ bool reb_tile(const DevArrays& a, int nreb, int w, TileCtx& t, SysParams& P) {
+  int lo = 0, hi = nreb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.reb_pref[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  t.sys = a.rebuild_ids[lo];
+  P = a.params[t.sys];
+  if (!P.active) return false;
+  t.tl = w - a.reb_pref[lo];
+  t.local = t.tl * kTile + (threadIdx.x & 31);
+  t.s = P.p_off + t.local;
+  t.act = t.local < P.n;
+  return true;
+}
+
+__device__ __forceinline__ int reb_systems(const DevArrays& a) { return a.ctl ? a.ctl->nreb : a.nreb; }
+
+// Rebuild passes visit only the tiles of the rebuilding systems, each warp
+// striding over them (a grid sized to the GPU, not to the arena).
+template <class F>
+__device__ __forceinline__ void for_rebuild_tiles(const DevArrays& a, F&& body) {
+  const int nreb = reb_systems(a);
+  const int total = a.reb_pref[nreb];
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < total; w += nw) {
+    TileCtx t;
+    SysParams P;
+    if (reb_tile(a, nreb, w, t, P)) body(t, P);
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host <-> slots
@@ -102,21 +137,21 @@ __global__ void k_to_caller(DevArrays a, int cur, int which, double* __restrict_
 // --------------------------------------------------------- binning (Sec. 2.1)
 
 __global__ void k_cell_count(DevArrays a, int cur) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  // Positions are wrapped into [0, L) only here (at a list build): between
-  // builds they move freely so that the periodic images stored in the list
-  // stay valid.
-  double4_32a x = a.x[cur][t.s];
-  const double4_32a w = make_double4_32a(wrap_fast(x.x, P.L), wrap_fast(x.y, P.L), wrap_fast(x.z, P.L), 0.0);
-  if (w.x != x.x || w.y != x.y || w.z != x.z) a.x[cur][t.s] = w;
-  int c = 0;
-  if (P.nc > 1) {
-    c = cell_of(w, P.inv_cs, P.nc);
-    atomicAdd(&a.ccount[P.c_off + c], 1);
-  }
-  a.cell[t.s] = c;
+  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
+    if (!t.act) return;
+    // Positions are wrapped into [0, L) only here (at a list build): between
+    // builds they move freely so that the periodic images stored in the list
+    // stay valid.
+    const double4_32a x = a.x[cur][t.s];
+    const double4_32a w = make_double4_32a(wrap_fast(x.x, P.L), wrap_fast(x.y, P.L), wrap_fast(x.z, P.L), 0.0);
+    if (w.x != x.x || w.y != x.y || w.z != x.z) a.x[cur][t.s] = w;
+    int c = 0;
+    if (P.nc > 1) {
+      c = cell_of(w, P.inv_cs, P.nc);
+      atomicAdd(&a.ccount[P.c_off + c], 1);
+    }
+    a.cell[t.s] = c;
+  });
 }
 
 // Exclusive scan of the cell counts of one rebuilding system per block (blocks
@@ -182,16 +217,16 @@ __global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
 }
 
 __global__ void k_scatter(DevArrays a) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  if (P.nc == 1) {
-    a.perm[t.s] = t.local;
-    return;
-  }
-  const int c = a.cell[t.s];
-  const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
-  a.perm[P.p_off + pos] = t.local;
+  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
+    if (!t.act) return;
+    if (P.nc == 1) {
+      a.perm[t.s] = t.local;
+      return;
+    }
+    const int c = a.cell[t.s];
+    const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
+    a.perm[P.p_off + pos] = t.local;
+  });
 }
 
 // Order the particles of each cell by x, ties by caller index (deterministic).
@@ -201,59 +236,59 @@ __global__ void k_scatter(DevArrays a) {
 // smaller key (x bits, then caller index), counted over the scattered members.
 // The first member of each cell resets the cell's fill counter.
 __global__ void k_cell_rank(DevArrays a, int cur) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  const int32_t* pm = a.perm + P.p_off;
-  const int p = t.local;  // position in the scattered order
-  const int i = pm[p];    // the particle's slot before the rebuild
-  if (P.nc == 1) {
-    a.perm2[t.s] = i;
-    return;
-  }
-  const int c = a.cell[P.p_off + i];
-  const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
-  if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
-  const double4_32a* xs = a.x[cur] + P.p_off;
-  const int32_t* id = a.id + P.p_off;
-  // keys: x >= 0 (wrapped), so its bit pattern orders like the value
-  const long long ki = __double_as_longlong(xs[i].x);
-  const int32_t idi = id[i];
-  int rank = 0;
-  for (int q = lo; q < hi; ++q) {
-    const int j = pm[q];
-    const long long kj = __double_as_longlong(xs[j].x);
-    rank += (kj < ki || (kj == ki && id[j] < idi)) ? 1 : 0;
-  }
-  a.perm2[P.p_off + lo + rank] = i;
+  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
+    if (!t.act) return;
+    const int32_t* pm = a.perm + P.p_off;
+    const int p = t.local;  // position in the scattered order
+    const int i = pm[p];    // the particle's slot before the rebuild
+    if (P.nc == 1) {
+      a.perm2[t.s] = i;
+      return;
+    }
+    const int c = a.cell[P.p_off + i];
+    const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
+    if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    const int32_t* id = a.id + P.p_off;
+    // keys: x >= 0 (wrapped), so its bit pattern orders like the value
+    const long long ki = __double_as_longlong(xs[i].x);
+    const int32_t idi = id[i];
+    int rank = 0;
+    for (int q = lo; q < hi; ++q) {
+      const int j = pm[q];
+      const long long kj = __double_as_longlong(xs[j].x);
+      rank += (kj < ki || (kj == ki && id[j] < idi)) ? 1 : 0;
+    }
+    a.perm2[P.p_off + lo + rank] = i;
+  });
 }
 
 __global__ void k_gather(DevArrays a, int cur) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  const int64_t old = P.p_off + a.perm2[t.s];
-  a.xtmp[t.s] = a.x[cur][old];
-  a.vtmp[t.s] = a.v[old];
-  a.idtmp[t.s] = a.id[old];
-  a.celltmp[t.s] = a.cell[old];
+  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
+    if (!t.act) return;
+    const int64_t old = P.p_off + a.perm2[t.s];
+    a.xtmp[t.s] = a.x[cur][old];
+    a.vtmp[t.s] = a.v[old];
+    a.idtmp[t.s] = a.id[old];
+    a.celltmp[t.s] = a.cell[old];
+  });
 }
 
 __global__ void k_copyback(DevArrays a, int cur) {
-  TileCtx t;
-  SysParams P;
-  if (!tile_ctx(a, t, P) || !a.rebuild[t.sys] || !t.act) return;
-  const double4_32a x = a.xtmp[t.s];
-  a.x[cur][t.s] = x;
-  a.xref[t.s] = x;
-  int4 q = fixed4(x, P.qscale);
-  a.xqref[t.s] = q;
-  q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
-  a.xq[cur][t.s] = q;
-  a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
-  a.v[t.s] = a.vtmp[t.s];
-  a.id[t.s] = a.idtmp[t.s];
-  a.cell[t.s] = a.celltmp[t.s];
+  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
+    if (!t.act) return;
+    const double4_32a x = a.xtmp[t.s];
+    a.x[cur][t.s] = x;
+    a.xref[t.s] = x;
+    int4 q = fixed4(x, P.qscale);
+    a.xqref[t.s] = q;
+    q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
+    a.xq[cur][t.s] = q;
+    a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
+    a.v[t.s] = a.vtmp[t.s];
+    a.id[t.s] = a.idtmp[t.s];
+    a.cell[t.s] = a.celltmp[t.s];
+  });
 }
 
 // ----------------------------------------------- pair list (Sec. 2.1, Fig. 1)
@@ -516,27 +551,51 @@ __device__ __forceinline__ void list_done(const DevArrays& a, int sys, int64_t s
 
 }  // namespace
 
+namespace {
+
+// Next tile of the rebuilding systems for this warp, from a shared work counter
+// (dynamic: tiles differ in cost); false when none is left. Warp-uniform.
+__device__ __forceinline__ bool next_rebuild_tile(const DevArrays& a, int& sys, int& tl) {
+  const int nreb = reb_systems(a);
+  const int total = a.reb_pref[nreb];
+  int w = 0;
+  if ((threadIdx.x & 31) == 0) w = atomicAdd(a.tile_next, 1);
+  w = __shfl_sync(kFull, w, 0);
+  if (w >= total) return false;
+  int lo = 0, hi = nreb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.reb_pref[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  sys = a.rebuild_ids[lo];
+  tl = w - a.reb_pref[lo];
+  return true;
+}
+
+}  // namespace
+
 template <int BLOCK, int VAR>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a, int cur) {
   constexpr int PRE = VAR & 1;
   constexpr bool kPrune = (VAR & 2) != 0;
-  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp >= a.ntiles) return;
-  const int sys = a.tile_sys[warp];
-  if (sys < 0 || !a.rebuild[sys]) return;
-  const SysParams* __restrict__ Pp = a.params + sys;
-  if (!Pp->active) return;
-  const int tl = warp - Pp->t_off;
-  const int li = tl * kTile + lane;
-  const int n = Pp->n;
-  if (li >= n) return;
-  const int64_t p_off = Pp->p_off;
-  const int kmax = Pp->kmax;
-  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
-  if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
-  else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
-  list_done(a, sys, p_off + li, o.count, kmax, true, __activemask(), lane);
+  int sys, tl;
+  while (next_rebuild_tile(a, sys, tl)) {
+    const SysParams* __restrict__ Pp = a.params + sys;
+    if (!Pp->active) continue;
+    const int li = tl * kTile + lane;
+    const int n = Pp->n;
+    const bool act = li < n;
+    const int64_t p_off = Pp->p_off;
+    const int kmax = Pp->kmax;
+    ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
+    if (act) {
+      if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+      else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
+    }
+    list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+  }
 }
 
 // Warp-cooperative list build: the same lists, in the same order, as
@@ -550,17 +609,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
 // than the cell side >= rl, so they fail its test; every cell of the union
 // appears once, with one image, because a group spans at most nc - 2 cells
 // (wider runs of a row are split into several groups). Full lists only.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArrays a, int cur) {
-  __shared__ float4 sbuf[BLOCK];
-  const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+namespace {
+
+__device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int sys, int tl, float4* buf) {
   const int lane = threadIdx.x & 31;
-  if (warp >= a.ntiles) return;  // every return above the loop is uniform over the warp
-  const int sys = a.tile_sys[warp];
-  if (sys < 0 || !a.rebuild[sys]) return;
   const SysParams* __restrict__ Pp = a.params + sys;
-  if (!Pp->active) return;
-  const int tl = warp - Pp->t_off;
+  if (!Pp->active) return;  // every return above the loop is uniform over the warp
   const int li = tl * kTile + lane;
   const int n = Pp->n;
   const bool act = li < n;
@@ -574,7 +628,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArra
     list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
     return;
   }
-  float4* buf = sbuf + (threadIdx.x & ~31);
   const float4* __restrict__ xf = a.xf + p_off;
   const int32_t* __restrict__ cst = a.cstart + Pp->c_off;
   const double L = Pp->L;
@@ -682,6 +735,16 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArra
     }
   }
   list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+}
+
+}  // namespace
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArrays a, int cur) {
+  __shared__ float4 sbuf[BLOCK];
+  float4* buf = sbuf + (threadIdx.x & ~31);
+  int sys, tl;
+  while (next_rebuild_tile(a, sys, tl)) build_tile_warp(a, cur, sys, tl, buf);
 }
 
 // ------------------------------------- fused force + velocity-Verlet step
@@ -1219,7 +1282,7 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
 // body (last), of the loop node (h_loop). A non-finite position or velocity
 // stops the loop (abort word 2).
 __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32, int vflag, int32_t* rebuild,
-                                                 int32_t* rebuild_ids, int32_t* reb_count,
+                                                 int32_t* rebuild_ids, int32_t* reb_pref, int32_t* reb_count,
                                                  cudaGraphConditionalHandle h_if,
                                                  cudaGraphConditionalHandle h_loop, int last) {
   GraphCtl* c = a.ctl;
@@ -1286,8 +1349,40 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     if (threadIdx.x == 0) base_s += total_s;
     __syncthreads();
   }
+  // prefix of the rebuilding systems' tile counts (the rebuild kernels' work list)
+  const int nreb_all = base_s;
+  int carry = 0;
+  for (int r0 = 0; r0 < nreb_all; r0 += 1024) {
+    const int r = r0 + (int)threadIdx.x;
+    const int v = r < nreb_all ? a.params[rebuild_ids[r]].ntiles : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int ws = wsum[lane];
+      int wi = ws;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, wi, o);
+        if (lane >= o) wi += y;
+      }
+      wsum[lane] = wi - ws;
+      if (lane == 31) total_s = wi;
+    }
+    __syncthreads();
+    if (r < nreb_all) reb_pref[r] = carry + wsum[w] + incl - v;
+    carry += total_s;
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     const int nreb = base_s;
+    reb_pref[nreb] = carry;
+    *a.tile_next = 0;
     c->done += 1;
     if (bad_s) {
       c->abort = 2;
@@ -1308,24 +1403,30 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
 }
 
 void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* rebuild, int32_t* rebuild_ids,
-                   int32_t* reb_count, cudaGraphConditionalHandle h_if, cudaGraphConditionalHandle h_loop,
-                   int last, cudaStream_t s) {
-  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_count, h_if, h_loop, last);
+                   int32_t* reb_pref, int32_t* reb_count, cudaGraphConditionalHandle h_if,
+                   cudaGraphConditionalHandle h_loop, int last, cudaStream_t s) {
+  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_pref, reb_count, h_if, h_loop, last);
+}
+
+// Binning kernels of a rebuild pass: at most 16 blocks of 128 per SM; warps stride
+// over the rebuilding systems' tiles.
+inline unsigned bin_blocks(const DevArrays& a) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.ntiles + 3) / 4, 152 * 16));
 }
 
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
-  k_cell_count<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+  k_cell_count<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
   k_cell_scan<<<(unsigned)std::min(std::max(nreb, 1), 1024), 1024, 0, s>>>(a, nreb);
 }
-void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<tile_blocks(a), kBlock, 0, s>>>(a); }
+void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<bin_blocks(a), kBlock, 0, s>>>(a); }
 void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s) {
-  k_cell_rank<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+  k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
-void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<tile_blocks(a), kBlock, 0, s>>>(a, cur); }
+void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<bin_blocks(a), kBlock, 0, s>>>(a, cur); }
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
-  k_copyback<<<tile_blocks(a), kBlock, 0, s>>>(a, cur);
+  k_copyback<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 namespace {
 inline unsigned blocks_of(const DevArrays& a, int block) {
@@ -1333,12 +1434,21 @@ inline unsigned blocks_of(const DevArrays& a, int block) {
 }
 }  // namespace
 
+// Rebuild passes: warps stride over (or fetch) the rebuilding systems' tiles, so
+// the grids are sized to the GPU (two waves of resident warps) or to the arena's
+// tiles if fewer.
+constexpr int kSMs = 152;
+inline unsigned reb_blocks(const DevArrays& a, int block, int blocks_per_sm) {
+  const int64_t all = ((int64_t)a.ntiles * kTile + block - 1) / block;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(all, (int64_t)kSMs * blocks_per_sm * 2));
+}
+
 template <int VAR>
 static void launch_build_list_v(const DevArrays& a, int cur, int block, cudaStream_t s) {
   switch (block) {
-    case 64: k_build_list<64, VAR><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
-    case 256: k_build_list<256, VAR><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
-    default: k_build_list<128, VAR><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+    case 64: k_build_list<64, VAR><<<reb_blocks(a, 64, 16), 64, 0, s>>>(a, cur); break;
+    case 256: k_build_list<256, VAR><<<reb_blocks(a, 256, 4), 256, 0, s>>>(a, cur); break;
+    default: k_build_list<128, VAR><<<reb_blocks(a, 128, 8), 128, 0, s>>>(a, cur); break;
   }
 }
 
@@ -1346,9 +1456,9 @@ void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream
   switch (tu.list_variant) {
     case 4:
       switch (tu.list_block) {
-        case 64: k_build_list_warp<64><<<blocks_of(a, 64), 64, 0, s>>>(a, cur); break;
-        case 256: k_build_list_warp<256><<<blocks_of(a, 256), 256, 0, s>>>(a, cur); break;
-        default: k_build_list_warp<128><<<blocks_of(a, 128), 128, 0, s>>>(a, cur); break;
+        case 64: k_build_list_warp<64><<<reb_blocks(a, 64, 16), 64, 0, s>>>(a, cur); break;
+        case 256: k_build_list_warp<256><<<reb_blocks(a, 256, 4), 256, 0, s>>>(a, cur); break;
+        default: k_build_list_warp<128><<<reb_blocks(a, 128, 8), 128, 0, s>>>(a, cur); break;
       }
       break;
     case 1: launch_build_list_v<1>(a, cur, tu.list_block, s); break;
