@@ -331,6 +331,15 @@ struct ListCtx {
     if (p && count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
     count += p ? 1 : 0;
   }
+  __device__ __forceinline__ void push(uint32_t e) {
+    if (count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
+    ++count;
+  }
+  // Whether candidate j with image code (not 0xff) passes the exact FP64 test.
+  __device__ __forceinline__ bool exact_in(int j, unsigned code) const {
+    const double4_32a xi = xs[li], xj = xs[j];
+    return (exact_inside(xi.x, xi.y, xi.z, xj.x, xj.y, xj.z, code, Pp->L, Pp->rl2) >> 8) & 1u;
+  }
   // The exact FP64 test of candidate j with image code (0xff: minimum image).
   __device__ __forceinline__ void exact(int j, unsigned code) {
     const double4_32a xi = xs[li], xj = xs[j];
@@ -384,9 +393,12 @@ __device__ __forceinline__ float key_of(const int4& q) { return __int_as_float(q
 // particle and append the partners in candidate order. The range is ordered by x
 // (float key) and only the window xlo <= x_j < xhi can hold partners: the first
 // candidate is found by bisection and the sweep stops past xhi. Candidates are
-// taken four at a time (independent loads; the slot arrays have four spare
-// entries, masked off, at the end); when the pre-test decides all four the
-// appends are predicated stores, otherwise the four take the exact test in order.
+// taken in windows of 32 (eight groups of four independent loads; the slot
+// arrays have four spare entries at the end): the pre-test sets a bit per
+// candidate that is surely inside and per candidate that may be inside; the
+// range end, the particle itself and (half list) the lower slots are masked once
+// per window, the rare shell candidates take the exact test, and the accepted
+// ones are appended in order.
 template <int PRE>
 __device__ __forceinline__ void sweep_range(const PreTest<PRE>& T, ListCtx& o, int lo, int hi, unsigned code,
                                             float xlo, float xhi) {
@@ -397,31 +409,52 @@ __device__ __forceinline__ void sweep_range(const PreTest<PRE>& T, ListCtx& o, i
     else b = m;
   }
   const uint32_t cbits = code << kIdxBits;
-  for (int j = lo; j < hi; j += 4) {
-    const auto q0 = T.load(j), q1 = T.load(j + 1), q2 = T.load(j + 2), q3 = T.load(j + 3);
-    if (!(key_of(q0) < xhi)) break;
-    const float r0 = T.r2(q0), r1 = T.r2(q1), r2 = T.r2(q2), r3 = T.r2(q3);
-    unsigned m = (r0 < T.hi2 ? 1u : 0u) | (r1 < T.hi2 ? 2u : 0u) | (r2 < T.hi2 ? 4u : 0u) | (r3 < T.hi2 ? 8u : 0u);
-    m &= (hi - j) >= 4 ? 15u : ((1u << (hi - j)) - 1u);
-    if ((unsigned)(o.li - j) < 4u) m &= ~(1u << (o.li - j));  // not the particle itself
-    if (o.half) {  // half list: keep candidates j + k > li
-      const int d = o.li - j;
-      if (d >= 3) m = 0u;
-      else if (d >= 0) m &= ~((2u << d) - 1u);
-    }
-    if (m) {
-      const unsigned in = m & ((r0 < T.lo2 ? 1u : 0u) | (r1 < T.lo2 ? 2u : 0u) | (r2 < T.lo2 ? 4u : 0u) |
-                               (r3 < T.lo2 ? 8u : 0u));
-      if (in == m) {
-        const uint32_t e = (uint32_t)j | cbits;
-        o.push_if(m & 1u, e);
-        o.push_if(m & 2u, e + 1);
-        o.push_if(m & 4u, e + 2);
-        o.push_if(m & 8u, e + 3);
-      } else {
-        for (int k = 0; k < 4; ++k)
-          if ((m >> k) & 1u) o.exact(j + k, code);
+  int j = lo;
+  bool more = j < hi;
+  while (more) {
+    const int j0 = j;
+    unsigned in = 0u, may = 0u;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if (more) {
+        const auto q0 = T.load(j), q1 = T.load(j + 1), q2 = T.load(j + 2), q3 = T.load(j + 3);
+        if (!(key_of(q0) < xhi)) {
+          more = false;
+        } else {
+          const float r0 = T.r2(q0), r1 = T.r2(q1), r2 = T.r2(q2), r3 = T.r2(q3);
+          if (r0 < T.hi2) may |= 1u << (4 * g);
+          if (r1 < T.hi2) may |= 2u << (4 * g);
+          if (r2 < T.hi2) may |= 4u << (4 * g);
+          if (r3 < T.hi2) may |= 8u << (4 * g);
+          if (r0 < T.lo2) in |= 1u << (4 * g);
+          if (r1 < T.lo2) in |= 2u << (4 * g);
+          if (r2 < T.lo2) in |= 4u << (4 * g);
+          if (r3 < T.lo2) in |= 8u << (4 * g);
+          j += 4;
+          more = j < hi;
+        }
       }
+    }
+    const int nt = min(j, hi) - j0;  // candidates tested in this window
+    unsigned valid = nt >= 32 ? ~0u : ((1u << nt) - 1u);
+    if ((unsigned)(o.li - j0) < 32u) valid &= ~(1u << (o.li - j0));  // not the particle itself
+    if (o.half) {  // half list: keep candidates above the particle's slot
+      const int d = o.li - j0;
+      if (d >= 31) valid = 0u;
+      else if (d >= 0) valid &= ~((2u << d) - 1u);
+    }
+    may &= valid;
+    in &= may;
+    unsigned shell = may & ~in;
+    while (shell) {  // between the pre-test's thresholds: the exact FP64 test
+      const int k = __ffs(shell) - 1;
+      shell &= shell - 1u;
+      if (o.exact_in(j0 + k, code)) in |= 1u << k;
+    }
+    while (in) {
+      const int k = __ffs(in) - 1;
+      in &= in - 1u;
+      o.push((uint32_t)(j0 + k) | cbits);
     }
   }
 }
@@ -1408,10 +1441,10 @@ void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* r
   k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_pref, reb_count, h_if, h_loop, last);
 }
 
-// Binning kernels of a rebuild pass: at most 16 blocks of 128 per SM; warps stride
+// Binning kernels of a rebuild pass: at most 64 blocks of 128 per SM; warps stride
 // over the rebuilding systems' tiles.
 inline unsigned bin_blocks(const DevArrays& a) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.ntiles + 3) / 4, 152 * 16));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.ntiles + 3) / 4, 152 * 64));
 }
 
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
