@@ -1186,7 +1186,9 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
       const double dz = apply_image(xj.z - xi.z, (code >> 4) & 3u, P.L);
       const double r2 = dx * dx + dy * dy + dz * dz;
       if (r2 < P.rc2) {
-        const double ir2 = 1.0 / r2;
+        // reciprocal within rounding in 3 DFMA (see rcp_f64); IEEE division only for
+        // (near-)coincident pairs, outside rcp_f64's range
+        const double ir2 = r2 > 1e-30 ? rcp_f64(r2) : 1.0 / r2;
         const double ir6 = ir2 * ir2 * ir2;
         pe += 4.0 * (ir6 * ir6 - ir6 + P.c2 * r2 + P.c0);
         w += 48.0 * ir6 * ir6 - 24.0 * ir6 - 8.0 * P.c2 * r2;
@@ -1332,7 +1334,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) { base_s = 0; bad_s = 0; }
   __syncthreads();
-  for (int k0 = 0; k0 < nsys; k0 += 1024) {
+  for (int k0 = 0; k0 < nsys; k0 += (int)blockDim.x) {
     const int k = k0 + (int)threadIdx.x;
     int need = 0;
     if (k < nsys) {
@@ -1361,7 +1363,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     if (lane == 0) wsum[w] = __popc(b);
     __syncthreads();
     if (w == 0) {
-      const int v = wsum[lane];
+      const int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
       int incl = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -1385,7 +1387,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
   // prefix of the rebuilding systems' tile counts (the rebuild kernels' work list)
   const int nreb_all = base_s;
   int carry = 0;
-  for (int r0 = 0; r0 < nreb_all; r0 += 1024) {
+  for (int r0 = 0; r0 < nreb_all; r0 += (int)blockDim.x) {
     const int r = r0 + (int)threadIdx.x;
     const int v = r < nreb_all ? a.params[rebuild_ids[r]].ntiles : 0;
     int incl = v;
@@ -1397,7 +1399,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     if (lane == 31) wsum[w] = incl;
     __syncthreads();
     if (w == 0) {
-      const int ws = wsum[lane];
+      const int ws = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
       int wi = ws;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -1438,7 +1440,10 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
 void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* rebuild, int32_t* rebuild_ids,
                    int32_t* reb_pref, int32_t* reb_count, cudaGraphConditionalHandle h_if,
                    cudaGraphConditionalHandle h_loop, int last, cudaStream_t s) {
-  k_decide<<<1, 1024, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_pref, reb_count, h_if, h_loop, last);
+  // one block; as many warps as the systems need (a single warp for one system)
+  const int threads = std::min(1024, (nsys + 31) / 32 * 32);
+  k_decide<<<1, threads, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_pref, reb_count, h_if, h_loop,
+                                 last);
 }
 
 // Binning kernels of a rebuild pass: at most 64 blocks of 128 per SM; warps stride
