@@ -239,6 +239,20 @@ def cpu_baseline(cfg, budget_s=20.0):
                       f"(initial list build excluded); single thread"}
 
 
+def replica_totals(dist, seconds: float, units: float, device: str = "cpu") -> tuple[float, float]:
+    """Whole-job figures of independent replicas: the slowest rank's time (max over
+    ranks) and the units every rank processed (sum over ranks). Without a process
+    group, this rank's own figures."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -262,20 +276,15 @@ def run_ours(args):
     r64 = time_form(ljmd, cfg, ljmd.MD_FP64, r64_steps, max(args.warmup // 4, 3), stream, clocks, dist)
     ck = clocks.stop()
 
-    def agg(ms):
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return ms
-
-    ms32 = agg(r32["ms"])
-    ms64 = agg(r64["ms"])
-    value = world * cfg.n * args.steps / (ms32 / 1e3)
-    value64 = world * cfg.n * r64_steps / (ms64 / 1e3)
+    sec32, units32 = replica_totals(dist, r32["ms"] / 1e3, float(cfg.n * args.steps), "cuda")
+    sec64, units64 = replica_totals(dist, r64["ms"] / 1e3, float(cfg.n * r64_steps), "cuda")
+    ms32, ms64 = sec32 * 1e3, sec64 * 1e3
+    value = units32 / sec32
+    value64 = units64 / sec64
 
     e2e = e2e_run(ljmd, cfg, ljmd.MD_FP32_FORCE, args.steps)
-    e2e_val = world * cfg.n * args.steps / e2e["seconds"]
+    e2e_sec, e2e_units = replica_totals(dist, e2e["seconds"], float(cfg.n * args.steps), "cuda")
+    e2e_val = e2e_units / e2e_sec
 
     batched = serve = None
     if not args.skip_batched and rank == 0:
