@@ -119,6 +119,20 @@ MD_API int md_set_pair_list(md_ctx* ctx, int kind);
  * v (N*3) from host memory; forces a list rebuild before the next force evaluation. */
 MD_API int md_set_state(md_ctx* ctx, const double* x, const double* v);
 
+/* Exact checkpoint for resuming a run bit for bit (the paper's product runs last many
+ * hours, Sec. 4.1). md_get_checkpoint copies into caller-allocated N*3 arrays the
+ * positions as held (between list builds positions are not wrapped, so that the
+ * periodic images stored in the list stay valid; they lie within L + skin of the box),
+ * the velocities and the positions at the last list build, and the velocity-bound
+ * margin (MD_RULE_DUTC). md_set_checkpoint restores them into a context with the same
+ * N, L, rc, skin, precision, rule and pair-list form: the list is rebuilt from the build
+ * positions (the same particle order and list as at that build) and the positions as
+ * held are put back, so that the following steps equal those of the uninterrupted run.
+ * Errors: MD_ERR_ARG, MD_ERR_STATE (no state to checkpoint), MD_ERR_CUDA. */
+MD_API int md_get_checkpoint(md_ctx* ctx, double* x, double* v, double* x_build, double* margin);
+MD_API int md_set_checkpoint(md_ctx* ctx, const double* x, const double* v, const double* x_build,
+                             double margin);
+
 /* Same with device pointers (N*3 float64 each), ordered on stream. */
 MD_API int md_set_state_dev(md_ctx* ctx, const double* x_dev, const double* v_dev, void* stream);
 

@@ -123,6 +123,44 @@ int md_set_state_dev(md_ctx* c, const double* x, const double* v, void* stream) 
   return c->eng.set_state_dev(0, x, v, (cudaStream_t)stream);
 }
 
+int md_get_checkpoint(md_ctx* c, double* x, double* v, double* xref, double* margin) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!x || !v || !xref || !margin) {
+    set_error("null checkpoint array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = n_of(c);
+  double* st = nullptr;
+  if ((r = c->eng.stage(n, &st))) return r;
+  // two arrays at a time through the staging buffer (6 n doubles)
+  double m = 0.0;
+  if ((r = c->eng.get_checkpoint_dev(0, nullptr, nullptr, st, &m, c->stream))) return r;
+  if ((r = d2h(c, xref, st, 3 * n))) return r;
+  if ((r = c->eng.get_checkpoint_dev(0, st, st + 3 * n, nullptr, nullptr, c->stream))) return r;
+  if ((r = d2h(c, x, st, 3 * n))) return r;
+  if ((r = d2h(c, v, st + 3 * n, 3 * n))) return r;
+  *margin = m;
+  return MD_OK;
+}
+
+int md_set_checkpoint(md_ctx* c, const double* x, const double* v, const double* xref, double margin) {
+  int r = check_ctx(c);
+  if (r) return r;
+  if (!x || !v || !xref) {
+    set_error("null checkpoint array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = n_of(c);
+  double* st = nullptr;
+  if ((r = c->eng.stage(n, &st))) return r;
+  if ((r = h2d(c, st, xref, 3 * n))) return r;
+  if ((r = h2d(c, st + 3 * n, v, 3 * n))) return r;
+  if ((r = c->eng.set_checkpoint_dev(0, st, st + 3 * n, c->stream))) return r;
+  if ((r = h2d(c, st, x, 3 * n))) return r;
+  return c->eng.finish_checkpoint_dev(0, st, margin, c->stream);
+}
+
 int md_get_state(md_ctx* c, double* x, double* v) {
   int r = check_ctx(c);
   if (r) return r;

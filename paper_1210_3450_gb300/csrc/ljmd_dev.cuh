@@ -177,6 +177,7 @@ void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, cons
                        cudaStream_t s);
 void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n,
                       int sys, int64_t ntiles_sys, cudaStream_t s);
+void launch_positions_by_id(const DevArrays& a, int cur, const double* x, int64_t sys_n, int sys, cudaStream_t s);
 void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v,
                         int sys, int64_t ntiles_sys, cudaStream_t s);
 

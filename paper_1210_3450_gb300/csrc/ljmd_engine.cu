@@ -1037,6 +1037,41 @@ int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) 
   return kOK;
 }
 
+int Engine::get_checkpoint_dev(int k, double* x, double* v, double* xref, double* margin, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  SysHost& h = sys_[k];
+  if (!h.has_state) { set_error("no state set"); return kErrState; }
+  CKR(ensure_lists(s));  // a state set since the last build gets its list (and build positions) now
+  const DevArrays a = arrays();
+  if (x) launch_to_caller(a, cur_, 4, x, h.spec.n, k, h.ntiles, s);
+  if (v) launch_to_caller(a, cur_, 1, v, h.spec.n, k, h.ntiles, s);
+  if (xref) launch_to_caller(a, cur_, 5, xref, h.spec.n, k, h.ntiles, s);
+  CKL();
+  if (margin) CK(cudaMemcpyAsync(margin, d_margin_ + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return kOK;
+}
+
+// Restore, first part: the build positions and velocities, then the list built
+// from them.
+int Engine::set_checkpoint_dev(int k, const double* xref, const double* v, cudaStream_t s) {
+  CKR(set_state_dev(k, xref, v, s));
+  return rebuild(std::vector<int>{k}, s);
+}
+
+// Restore, second part: the positions as held (over the freshly built slots) and
+// the margin; forces are recomputed before the next step.
+int Engine::finish_checkpoint_dev(int k, const double* x, double margin, cudaStream_t s) {
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  SysHost& h = sys_[k];
+  launch_positions_by_id(arrays(), cur_, x, h.spec.n, k, s);
+  CKL();
+  CK(cudaMemcpyAsync(d_margin_ + k, &margin, sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  h.f_valid = false;
+  return kOK;
+}
+
 int Engine::forces_dev(int k, double* f, cudaStream_t s) {
   if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   CKR(ensure_lists(s));

@@ -109,6 +109,13 @@ class Engine {
   int set_state_dev(int k, const double* x, const double* v, cudaStream_t s);
   int get_state_dev(int k, double* x, double* v, cudaStream_t s);
   int forces_dev(int k, double* f, cudaStream_t s);
+  // Exact checkpoint of system k (device arrays, caller order): positions as held
+  // (not wrapped), velocities, positions at the last list build, and the
+  // velocity-bound margin. Restoring rebuilds the list from the build positions
+  // (the same slot order and list as at that build), then puts back the positions.
+  int get_checkpoint_dev(int k, double* x, double* v, double* xref, double* margin, cudaStream_t s);
+  int set_checkpoint_dev(int k, const double* xref, const double* v, cudaStream_t s);
+  int finish_checkpoint_dev(int k, const double* x, double margin, cudaStream_t s);
 
   // Advance every active system by nsteps steps of its own dt (dt per system id;
   // entries of inactive ids are ignored).

@@ -111,7 +111,8 @@ __global__ void k_from_caller(DevArrays a, int cur, const double* __restrict__ x
   }
 }
 
-// which: 0 = positions, 1 = velocities, 2 = stored forces, 3 = cells (as double)
+// which: 0 = positions (wrapped into [0, L)), 1 = velocities, 2 = stored forces,
+// 4 = positions as held (not wrapped), 5 = positions at the last list build
 __global__ void k_to_caller(DevArrays a, int cur, int which, double* __restrict__ out, int sys) {
   const SysParams P = a.params[sys];
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -126,6 +127,10 @@ __global__ void k_to_caller(DevArrays a, int cur, int which, double* __restrict_
     q.z = wrap_fast(q.z, P.L);
   } else if (which == 1) {
     q = a.v[s];
+  } else if (which == 4) {
+    q = a.x[cur][s];
+  } else if (which == 5) {
+    q = a.xref[s];
   } else {
     q = a.f[s];
   }
@@ -1289,6 +1294,24 @@ inline unsigned tile_blocks(const DevArrays& a) {
   return (unsigned)(((int64_t)a.ntiles * kTile + kBlock - 1) / kBlock);
 }
 }  // namespace
+
+// Positions as held (caller order, not wrapped) into the slots of a system whose
+// list was just built, with their fixed-point shadows: a restored checkpoint.
+__global__ void k_positions_by_id(DevArrays a, int cur, const double* __restrict__ x, int sys) {
+  const SysParams P = a.params[sys];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= P.n) return;
+  const int64_t s = P.p_off + l;
+  const int64_t i = a.id[s];
+  const double4_32a xv = make_double4_32a(x[3 * i + 0], x[3 * i + 1], x[3 * i + 2], 0.0);
+  a.x[cur][s] = xv;
+  a.xq[cur][s] = fixed4(xv, P.qscale);
+}
+
+void launch_positions_by_id(const DevArrays& a, int cur, const double* x, int64_t sys_n, int sys, cudaStream_t s) {
+  if (sys_n <= 0) return;
+  k_positions_by_id<<<(unsigned)((sys_n + 255) / 256), 256, 0, s>>>(a, cur, x, sys);
+}
 
 void launch_from_caller(const DevArrays& a, int cur, const double* x, const double* v, int sys,
                         int64_t ntiles_sys, cudaStream_t s) {

@@ -61,6 +61,8 @@ SIGNATURES = {
     "md_create": (C.c_int, [C.c_double, C.c_int64, C.c_double, C.c_double, C.POINTER(_P)]),
     "md_set_precision": (C.c_int, [_P, C.c_int]),
     "md_set_validity_rule": (C.c_int, [_P, C.c_int]),
+    "md_get_checkpoint": (C.c_int, [_P, _PD, _PD, _PD, C.POINTER(C.c_double)]),
+    "md_set_checkpoint": (C.c_int, [_P, _PD, _PD, _PD, C.c_double]),
     "md_set_pair_list": (C.c_int, [_P, C.c_int]),
     "md_set_state": (C.c_int, [_P, _PD, _PD]),
     "md_set_state_dev": (C.c_int, [_P, _P, _P, _P]),
@@ -213,6 +215,23 @@ class LJSystem:
 
     def set_pair_list(self, kind: int):
         _check(_lib.md_set_pair_list(self._h, int(kind)))
+
+    def checkpoint(self) -> dict:
+        """Exact checkpoint: positions as held (not wrapped), velocities, positions at
+        the last list build, velocity-bound margin."""
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        xb = np.empty((self.n, 3))
+        m = C.c_double()
+        _check(_lib.md_get_checkpoint(self._h, _pd(x), _pd(v), _pd(xb), C.byref(m)))
+        return dict(x=x, v=v, x_build=xb, margin=m.value)
+
+    def restore(self, ck: dict):
+        """Restore a checkpoint taken from a system with the same sizes and settings."""
+        x = _host3(ck["x"], self.n)
+        v = _host3(ck["v"], self.n)
+        xb = _host3(ck["x_build"], self.n)
+        _check(_lib.md_set_checkpoint(self._h, _pd(x), _pd(v), _pd(xb), float(ck["margin"])))
 
     def set_state(self, x, v):
         x = _host3(x, self.n)
