@@ -173,7 +173,10 @@ void launch_step_fp32(const DevArrays& a, int cur, double ka, double kb, int fla
 void launch_pe_virial(const DevArrays& a, int cur, int with_pairs, const int32_t* select, cudaStream_t s);
 void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s);
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s);
-void launch_reduce_obs(const DevArrays& a, int cur, int nsys, double* out3, const int32_t* select,
+// Per-system (PE, W, KE) sums into out3[3 sys] for the nsel systems listed in work
+// (ids, then the prefix of their 256-tile chunk counts; nchunks in total); chunk3
+// holds 3 doubles per chunk.
+void launch_reduce_obs(const DevArrays& a, const int32_t* work, int nsel, int nchunks, double* chunk3, double* out3,
                        cudaStream_t s);
 void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64_t sys_n,
                       int sys, int64_t ntiles_sys, cudaStream_t s);

@@ -285,8 +285,8 @@ void Engine::free_all() {
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
-  dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_);
-  hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_);
+  dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
+  hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_); hfree(h_obs_work_);
   drop_graphs();
   dfree(d_ctl_); dfree(d_reb_count_); hfree(h_ctl_); hfree(h_reb_count_);
   d_ = DevArrays{};
@@ -380,6 +380,9 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_rebuild_, 3 * ns + 1));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
+  CKR(dmalloc(&d_obs_work_, 2 * ns + 1));
+  CKR(dmalloc(&d_obs_chunk_, 3 * (T / 256 + ns + 1)));
+  CK(cudaMallocHost((void**)&h_obs_work_, sizeof(int32_t) * (2 * ns + 1)));
   CKR(dmalloc(&d_pairs_, 2 * ns));
   CK(cudaMemset(d_status_, 0, sizeof(SysStatus) * ns));
   CK(cudaMemset(d_disp2_, 0, sizeof(unsigned long long) * ns));
@@ -1092,7 +1095,17 @@ int Engine::observables(double* out3, cudaStream_t s, bool with_pairs, const int
     dsel = d_rebuild_;
   }
   launch_pe_virial(a, cur_, with_pairs ? 1 : 0, dsel, s);
-  launch_reduce_obs(a, cur_, nsys(), d_obs_, dsel, s);
+  // the systems to reduce and the prefix of their chunk counts
+  int nsel = 0, nchunks = 0;
+  for (int k = 0; k < nsys(); ++k)
+    if (sys_[k].used && sys_[k].active && (!select || select[k])) h_obs_work_[nsel++] = k;
+  for (int r = 0; r < nsel; ++r) {
+    h_obs_work_[nsel + r] = nchunks;
+    nchunks += (sys_[h_obs_work_[r]].ntiles + 255) / 256;
+  }
+  h_obs_work_[2 * nsel] = nchunks;
+  CK(cudaMemcpyAsync(d_obs_work_, h_obs_work_, sizeof(int32_t) * (2 * nsel + 1), cudaMemcpyHostToDevice, s));
+  launch_reduce_obs(a, d_obs_work_, nsel, nchunks, d_obs_chunk_, d_obs_, s);
   CKL();
   CK(cudaMemcpyAsync(h_obs_, d_obs_, sizeof(double) * 3 * nsys(), cudaMemcpyDeviceToHost, s));
   CKR(sync_check(s));

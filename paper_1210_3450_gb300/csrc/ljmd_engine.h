@@ -231,6 +231,9 @@ class Engine {
   int32_t* d_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;
+  int32_t* d_obs_work_ = nullptr;  // selected systems and their chunk prefix (observables)
+  int32_t* h_obs_work_ = nullptr;
+  double* d_obs_chunk_ = nullptr;  // chunk sums (3 doubles per 256 tiles)
   unsigned long long* d_pairs_ = nullptr;
   double* d_stage_ = nullptr;
   int64_t stage_n_ = 0;

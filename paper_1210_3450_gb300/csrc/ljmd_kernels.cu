@@ -1253,27 +1253,72 @@ __global__ void __launch_bounds__(kBlock) k_pair_stats(DevArrays a, int cur, uns
   }
 }
 
-// One block per system: fixed-order sum of its tile partials (deterministic).
-__global__ void __launch_bounds__(256) k_reduce_obs(DevArrays a, int nsys, double* out3,
-                                                   const int32_t* __restrict__ select) {
-  const int sys = blockIdx.x;
-  if (sys >= nsys) return;
-  const SysParams P = a.params[sys];
-  if (!P.active || (select && !select[sys])) return;
+// Per-system sums of the tile partials (PE, W, KE), in two deterministic stages
+// whose partition is relative to each system's first tile (so a system reduces
+// the same way alone and in a batch): chunks of 256 tiles, one block each, summed
+// by a fixed tree; then one block per system adds its chunk sums in order.
+// work: the selected systems' ids (nsel) followed by the prefix of their chunk
+// counts (nsel + 1).
+constexpr int kObsChunk = 256;
+
+__global__ void __launch_bounds__(kObsChunk) k_obs_chunks(DevArrays a, const int32_t* __restrict__ work, int nsel,
+                                                        double* __restrict__ chunk3) {
+  const int b = blockIdx.x;
+  const int32_t* cpref = work + nsel;
+  int lo = 0, hi = nsel - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cpref[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const int sys = work[lo];
+  const SysParams& P = a.params[sys];
+  const int q = (b - cpref[lo]) * kObsChunk + (int)threadIdx.x;  // tile within the system
+  __shared__ double sh[3][kObsChunk];
+  double pe = 0.0, w = 0.0, ke = 0.0;
+  if (q < P.ntiles) {
+    const double* o = a.tile_obs + (int64_t)(P.t_off + q) * 3;
+    pe = o[0];
+    w = o[1];
+    ke = o[2];
+  }
+  sh[0][threadIdx.x] = pe;
+  sh[1][threadIdx.x] = w;
+  sh[2][threadIdx.x] = ke;
+  __syncthreads();
+  for (int o = kObsChunk / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    chunk3[3 * b + 0] = sh[0][0];
+    chunk3[3 * b + 1] = sh[1][0];
+    chunk3[3 * b + 2] = sh[2][0];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_obs_final(const int32_t* __restrict__ work, int nsel,
+                                                 const double* __restrict__ chunk3, double* __restrict__ out3) {
+  const int r = blockIdx.x;
+  const int sys = work[r];
+  const int c0 = work[nsel + r], c1 = work[nsel + r + 1];
   __shared__ double sh[3][256];
   double pe = 0.0, w = 0.0, ke = 0.0;
-  for (int q = threadIdx.x; q < P.ntiles; q += blockDim.x) {
-    const double* o = a.tile_obs + (int64_t)(P.t_off + q) * 3;
-    pe += o[0];
-    w += o[1];
-    ke += o[2];
+  for (int c = c0 + (int)threadIdx.x; c < c1; c += 256) {
+    pe += chunk3[3 * c + 0];
+    w += chunk3[3 * c + 1];
+    ke += chunk3[3 * c + 2];
   }
   sh[0][threadIdx.x] = pe;
   sh[1][threadIdx.x] = w;
   sh[2][threadIdx.x] = ke;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
+    if ((int)threadIdx.x < o) {
       sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
       sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
@@ -1617,8 +1662,11 @@ void launch_scale_v(const DevArrays& a, const double* scale, cudaStream_t s) {
 void launch_pair_stats(const DevArrays& a, int cur, unsigned long long* out2, cudaStream_t s) {
   k_pair_stats<<<tile_blocks(a), kBlock, 0, s>>>(a, cur, out2);
 }
-void launch_reduce_obs(const DevArrays& a, int, int nsys, double* out3, const int32_t* select, cudaStream_t s) {
-  k_reduce_obs<<<nsys, 256, 0, s>>>(a, nsys, out3, select);
+void launch_reduce_obs(const DevArrays& a, const int32_t* work, int nsel, int nchunks, double* chunk3, double* out3,
+                       cudaStream_t s) {
+  if (nsel <= 0 || nchunks <= 0) return;
+  k_obs_chunks<<<nchunks, kObsChunk, 0, s>>>(a, work, nsel, chunk3);
+  k_obs_final<<<nsel, 256, 0, s>>>(work, nsel, chunk3, out3);
 }
 
 }  // namespace ljmd
