@@ -1130,29 +1130,35 @@ int Engine::step_nvt(int64_t nsteps, const std::vector<double>& dt, const std::v
     }
   }
   std::vector<double> o3((size_t)(3 * ns)), fac((size_t)ns, 1.0);
-  // zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G',
-  // G = (2 KE - g T) / Q with g = 3 (N - 1)
-  auto half = [&]() -> int {
+  // `halves` consecutive thermostat half steps from one kinetic-energy reduction:
+  // each is zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G'
+  // with G = (2 KE - g T) / Q, g = 3 (N - 1); a uniform scale multiplies KE by its
+  // square, so the next G needs no new reduction. One velocity scaling at the end.
+  auto thermostat = [&](int halves) -> int {
     CKR(observables(o3.data(), s, false));
     for (int k = 0; k < ns; ++k) {
       fac[(size_t)k] = 1.0;
       if (!sys_[k].active) continue;
       const double g = 3.0 * (double)(sys_[k].spec.n - 1);
       double ke = o3[(size_t)(3 * k + 2)];
-      zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
-      eta[k] += 0.5 * dt[k] * zeta[k];
-      const double sc = std::exp(-0.5 * dt[k] * zeta[k]);
-      fac[(size_t)k] = sc;
-      ke = ke * sc * sc;
-      zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
+      for (int h = 0; h < halves; ++h) {
+        zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
+        eta[k] += 0.5 * dt[k] * zeta[k];
+        const double sc = std::exp(-0.5 * dt[k] * zeta[k]);
+        fac[(size_t)k] *= sc;
+        ke = ke * sc * sc;
+        zeta[k] += 0.25 * dt[k] * (2.0 * ke - g * T[k]) / Q[k];
+      }
     }
     return scale_velocities(fac, s);
   };
   CKR(ensure_lists(s));
+  if (nsteps == 0) return kOK;
+  CKR(thermostat(1));
   for (int64_t it = 0; it < nsteps; ++it) {
-    CKR(half());
     CKR(step(1, dt, s));
-    CKR(half());
+    // the end of this step and the start of the next are consecutive half steps
+    CKR(thermostat(it + 1 < nsteps ? 2 : 1));
   }
   return kOK;
 }
