@@ -632,17 +632,31 @@ int Engine::set_list_kind(int kind) {
 
 int Engine::set_active(int k, bool on) {
   if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
-  if (sys_[k].active != on) {
-    sys_[k].active = on;
-    CKR(upload_params(k));
+  SysHost& h = sys_[k];
+  if (h.active == on) return kOK;
+  if (!on) {
+    h.park = cur_;  // its positions stay in this buffer while the others step
+  } else if (h.park >= 0) {
+    if (h.park != cur_) {
+      // the others advanced an odd number of steps: move its positions (and shadows)
+      // to the buffer the next launch reads (after all work in flight)
+      CK(cudaDeviceSynchronize());
+      const size_t nslot = (size_t)h.ntiles * kTile;
+      CK(cudaMemcpy(d_.x[cur_] + h.p_off, d_.x[h.park] + h.p_off, sizeof(double4_32a) * nslot,
+                    cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(d_.xq[cur_] + h.p_off, d_.xq[h.park] + h.p_off, sizeof(int4) * nslot,
+                    cudaMemcpyDeviceToDevice));
+    }
+    h.park = -1;
   }
-  return kOK;
+  h.active = on;
+  return upload_params(k);
 }
 
 int Engine::set_state_dev(int k, const double* x, const double* v, cudaStream_t s) {
   if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   SysHost& h = sys_[k];
-  launch_from_caller(arrays(), cur_, x, v, k, h.ntiles, s);
+  launch_from_caller(arrays(), cur_of(k), x, v, k, h.ntiles, s);
   CKL();
   h.has_state = true;
   h.force_rebuild = true;
@@ -654,8 +668,8 @@ int Engine::get_state_dev(int k, double* x, double* v, cudaStream_t s) {
   if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   SysHost& h = sys_[k];
   if (!h.has_state) { set_error("no state set"); return kErrState; }
-  if (x) launch_to_caller(arrays(), cur_, 0, x, h.spec.n, k, h.ntiles, s);
-  if (v) launch_to_caller(arrays(), cur_, 1, v, h.spec.n, k, h.ntiles, s);
+  if (x) launch_to_caller(arrays(), cur_of(k), 0, x, h.spec.n, k, h.ntiles, s);
+  if (v) launch_to_caller(arrays(), cur_of(k), 1, v, h.spec.n, k, h.ntiles, s);
   CKL();
   return kOK;
 }
@@ -1046,9 +1060,9 @@ int Engine::get_checkpoint_dev(int k, double* x, double* v, double* xref, double
   if (!h.has_state) { set_error("no state set"); return kErrState; }
   CKR(ensure_lists(s));  // a state set since the last build gets its list (and build positions) now
   const DevArrays a = arrays();
-  if (x) launch_to_caller(a, cur_, 4, x, h.spec.n, k, h.ntiles, s);
-  if (v) launch_to_caller(a, cur_, 1, v, h.spec.n, k, h.ntiles, s);
-  if (xref) launch_to_caller(a, cur_, 5, xref, h.spec.n, k, h.ntiles, s);
+  if (x) launch_to_caller(a, cur_of(k), 4, x, h.spec.n, k, h.ntiles, s);
+  if (v) launch_to_caller(a, cur_of(k), 1, v, h.spec.n, k, h.ntiles, s);
+  if (xref) launch_to_caller(a, cur_of(k), 5, xref, h.spec.n, k, h.ntiles, s);
   CKL();
   if (margin) CK(cudaMemcpyAsync(margin, d_margin_ + k, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1067,7 +1081,7 @@ int Engine::set_checkpoint_dev(int k, const double* xref, const double* v, cudaS
 int Engine::finish_checkpoint_dev(int k, const double* x, double margin, cudaStream_t s) {
   if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
   SysHost& h = sys_[k];
-  launch_positions_by_id(arrays(), cur_, x, h.spec.n, k, s);
+  launch_positions_by_id(arrays(), cur_of(k), x, h.spec.n, k, s);
   CKL();
   CK(cudaMemcpyAsync(d_margin_ + k, &margin, sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -1196,7 +1210,7 @@ int Engine::bubbles(int k, double side, double gas_density, int* ns_out, std::ve
     return r;
   }
   const double vol = std::pow(h.spec.L / (double)ns, 3);
-  launch_bubbles(arrays(), cur_, k, h.spec.n, (int)ns, h.spec.L, gas_density * vol, d_counts, d_parent, d_size,
+  launch_bubbles(arrays(), cur_of(k), k, h.spec.n, (int)ns, h.spec.L, gas_density * vol, d_counts, d_parent, d_size,
                  d_err, s);
   cudaError_t e = cudaGetLastError();
   std::vector<int32_t> parent((size_t)ncell);

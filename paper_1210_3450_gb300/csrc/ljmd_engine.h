@@ -39,6 +39,9 @@ struct SysHost {
   bool f_valid = false;
   int64_t rebuilds = 0, steps = 0;
   double dt = 0.0;
+  // Position buffer (0/1) of an inactive system: launches advance the other
+  // systems' buffers in turn while its positions stay put; -1 = follows the engine.
+  int park = -1;
 };
 
 struct ArenaCaps {
@@ -181,6 +184,8 @@ class Engine {
   int run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s);
   int sync_check(cudaStream_t s);
   DevArrays arrays() const;
+  // Buffer holding system k's current positions.
+  int cur_of(int k) const { return (!sys_[k].active && sys_[k].park >= 0) ? sys_[k].park : cur_; }
   // Tuning of the list build (the warp-cooperative variant builds full lists only).
   Tuning list_tuning() const {
     Tuning t = tuning_;

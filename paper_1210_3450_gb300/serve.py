@@ -67,6 +67,7 @@ class Request:
     finished: float = math.nan
     remaining: int = 0
     sid: int = -1
+    active: bool = True
     result: dict = field(default_factory=dict)
 
     @property
@@ -86,8 +87,19 @@ class MDServer:
 
     def __init__(self, budget_bytes: int, precision: int = ljmd.MD_FP32_FORCE, chunk: int = 100,
                  max_systems: int = 4096, keep_state: bool = False, clock=time.perf_counter,
-                 prepare_threads: int = 4):
+                 prepare_threads: int = 4, policy: str = "shared", active_particles: int = 2_500_000):
+        """policy "shared": every admitted run advances in every chunk; "srpt": each
+        chunk advances the runs with the least remaining work (particles x steps),
+        smallest first, until `active_particles` are active (at least one run) and
+        the others wait on the device. Pausing a run does not change its result."""
+        if policy not in ("shared", "srpt"):
+            raise ValueError("policy must be 'shared' or 'srpt'")
+        self.policy = policy
+        self.active_particles = int(active_particles)
         self.arena = arena_for_budget(budget_bytes, max_systems)
+        # list words kept free at admission, so that admitted runs can grow their
+        # lists (a denser region raises a run's partner count)
+        self.list_reserve = self.arena["list_words"] // 20
         self.batch = ljmd.LJBatch(arena=self.arena, precision=precision)
         self.chunk = int(chunk)
         self.keep_state = keep_state
@@ -126,33 +138,60 @@ class MDServer:
         """FIFO admission; up to `backfill` later requests may pass a head that does
         not fit yet (smaller runs use the space it cannot)."""
         skipped = 0
+        free_list = self.batch.usage()["list_words_free"]
         for r in list(self.pending):
-            sid = self.batch.try_add(r.n, r.box, r.rc, r.skin)
+            need = ljmd.footprint(r.n, r.box, r.rc, r.skin)["list_words"]
+            sid = None
+            if free_list - need >= self.list_reserve or not self.running:
+                sid = self.batch.try_add(r.n, r.box, r.rc, r.skin)
             if sid is None:
                 skipped += 1
                 if skipped > backfill:
                     break
                 continue
+            free_list -= need
             fut = self.prepared.pop(id(r), None)
             x, v = fut.result() if fut is not None else initial_state(r)
             self.batch.set_state(sid, x, v)
             r.sid = sid
             r.admitted = now
             r.remaining = r.steps
+            r.active = True
             self.running[sid] = r
             self.pending.remove(r)
         self._prepare_ahead()
 
+    def _select_active(self) -> list[int]:
+        """The runs to advance in this chunk (and set the others inactive)."""
+        if self.policy == "shared":
+            return list(self.running)
+        order = sorted(self.running, key=lambda sid: (self.running[sid].n * self.running[sid].remaining, sid))
+        active, total = [], 0
+        for sid in order:
+            if active and total >= self.active_particles:
+                break
+            active.append(sid)
+            total += self.running[sid].n
+        chosen = set(active)
+        for sid, r in self.running.items():
+            on = sid in chosen
+            if r.active != on:
+                self.batch.set_active(sid, on)
+                r.active = on
+        return active
+
     def step_chunk(self) -> int:
         if not self.running:
             return 0
-        k = min(self.chunk, min(r.remaining for r in self.running.values()))
+        active = self._select_active()
+        k = min(self.chunk, min(self.running[sid].remaining for sid in active))
         dts = {sid: r.dt for sid, r in self.running.items()}
         t = self.clock()
         self.batch.step(k, dts)
         self.gpu_busy += self.clock() - t
         finished = []
-        for sid, r in self.running.items():
+        for sid in active:
+            r = self.running[sid]
             r.remaining -= k
             self.particle_steps += r.n * k
             if r.remaining == 0:

@@ -160,15 +160,16 @@ def mean_request_work() -> float:
     return en * 5500.0
 
 
-def serve_run(rate, duration, budget_gb=100.0, chunk=100, drain_limit=None, precision=1) -> dict:
+def serve_run(rate, duration, budget_gb=100.0, chunk=100, drain_limit=None, precision=1,
+              policy="shared") -> dict:
     from . import ljmd, serve
     reqs = serve.requests_from_workload(rate, duration)
-    srv = serve.MDServer(int(budget_gb * 1e9), precision, chunk=chunk)
+    srv = serve.MDServer(int(budget_gb * 1e9), precision, chunk=chunk, policy=policy)
     try:
         out = srv.run(reqs, drain_limit=drain_limit)
     finally:
         srv.close()
-    out.update(rate=rate, duration=duration, budget_gb=budget_gb, chunk=chunk,
+    out.update(rate=rate, duration=duration, budget_gb=budget_gb, chunk=chunk, policy=policy,
                offered_particle_steps_per_s=rate * mean_request_work())
     return out
 

@@ -135,3 +135,34 @@ def test_replica_workload_sample_matches_alone(ljmd):
                 xr, vr = m.get_state()
             np.testing.assert_array_equal(x, xr)
             np.testing.assert_array_equal(v, vr)
+
+
+@pytest.mark.parametrize("graph", [0, 1], ids=["host-loop", "graph"])
+def test_paused_system_resumes_exactly(ljmd, graph):
+    """A system set inactive while the others advance an odd number of steps (the
+    position buffers alternate by step) resumes from its own positions: its run
+    equals the run alone bit for bit."""
+    import lj_inputs as li
+    x1, b1 = li.perturbed_fcc(2000, 0.8, 0.08, 1201)
+    v1 = li.maxwell_boltzmann(2000, 1.0, 1202)
+    x2, b2 = li.perturbed_fcc(1500, 0.75, 0.08, 1203)
+    v2 = li.maxwell_boltzmann(1500, 1.0, 1204)
+    b = ljmd.LJBatch(systems=[(2000, b1, 2.5, 0.3), (1500, b2, 2.5, 0.3)], precision=ljmd.MD_FP32_FORCE)
+    try:
+        b.set_tuning(graph=graph)
+        b.set_state(0, x1, v1)
+        b.set_state(1, x2, v2)
+        b.step(20, [0.005, 0.005])
+        b.set_active(1, False)
+        b.step(7, [0.005, 0.005])          # system 0 only, odd count
+        b.set_active(1, True)
+        b.step(33, [0.005, 0.005])
+        xb, vb = b.get_state(1)
+    finally:
+        b.close()
+    with ljmd.LJSystem(b2, 1500, 2.5, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state(x2, v2)
+        s.step(53, 0.005)
+        xa, va = s.get_state()
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(va, vb)

@@ -7,7 +7,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone(ljmd):
+@pytest.mark.parametrize("policy", ["shared", "srpt"])
+def test_served_results_equal_alone(ljmd, policy):
     from paper_1210_3450_gb300 import serve
     reqs = []
     rng = np.random.default_rng(5)
@@ -18,7 +19,8 @@ def test_served_results_equal_alone(ljmd):
                                   steps=int(rng.integers(30, 150)), seed=1000 + k))
     # budget for roughly three of these runs at a time: later ones must wait
     budget = 3 * 5000 * 900
-    srv = serve.MDServer(budget, precision=ljmd.MD_FP32_FORCE, chunk=40, keep_state=True)
+    srv = serve.MDServer(budget, precision=ljmd.MD_FP32_FORCE, chunk=40, keep_state=True, policy=policy,
+                         active_particles=6000)
     try:
         summary = srv.run(reqs)
     finally:
