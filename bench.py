@@ -124,9 +124,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
+# the device code of the profiled kernels (host code cannot change their traffic)
+KERNEL_SOURCES = ("ljmd_kernels.cu", "ljmd_dev.cuh", "ljmd_math.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1210_3450_gb300", "csrc"))):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1210_3450_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
