@@ -323,7 +323,12 @@ MD_API int md_batch_remove(md_batch* b, int id);
  * list words free, system records, systems in use. */
 MD_API int md_batch_usage(md_batch* b, int64_t* out8);
 
-/* Include (on = 1) or exclude (on = 0) a system from md_batch_step. */
+/* Include (on = 1) or exclude (on = 0) a system from md_batch_step and
+ * md_batch_observables (which report zeros for it). An excluded system keeps its state
+ * untouched, however many steps the others take, and continues exactly where it stopped
+ * when included again: a paused run's result equals its uninterrupted run. Its state
+ * can still be read and set while excluded; md_batch_forces returns its forces from its
+ * last step. */
 MD_API int md_batch_set_active(md_batch* b, int id, int on);
 
 MD_API int md_batch_set_precision(md_batch* b, int mode);
