@@ -329,7 +329,6 @@ int Engine::init_arena(const ArenaCaps& caps, int precision) {
   list_alloc_.reset(caps_.list_words / (4 * kTile));  // in 128-word units
   h_tile_sys_.assign((size_t)(caps_.slots / kTile), -1);
   ntiles_ = 0;
-  max_cells_ = 1;
   cur_ = 0;
   return alloc_arrays();
 }
@@ -414,11 +413,9 @@ int Engine::stage(int64_t n, double** out) {
 
 void Engine::update_extent() {
   int32_t last = 0;
-  max_cells_ = 1;
   for (const SysHost& h : sys_) {
     if (!h.used) continue;
     last = std::max(last, h.t_off + h.ntiles);
-    max_cells_ = std::max(max_cells_, h.ncell);
   }
   ntiles_ = last;
   ++struct_ver_;

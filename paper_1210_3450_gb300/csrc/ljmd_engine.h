@@ -224,7 +224,6 @@ class Engine {
   ArenaCaps caps_{0, 0, 0, 0};
   bool list_growable_ = false;  // exact-size arenas grow their list storage on demand
   RangeAlloc slot_alloc_, cell_alloc_, list_alloc_;
-  int64_t max_cells_ = 1;
   int32_t ntiles_ = 0;  // launch extent: tiles up to the last used one
   std::vector<int32_t> h_tile_sys_;
 
