@@ -267,3 +267,45 @@ def test_full_size_sampled_forces(ljmd, oracle):
         rms = np.sqrt((f ** 2).sum(1).mean())
         assert np.abs(f.sum(0)).max() <= (1e-12 if precision == 0 else 1e-4) * len(x) * rms
         assert 70 * len(x) < n_list < 90 * len(x)
+
+
+def test_cavitation_size_sampled_forces(ljmd, oracle):
+    """The cavitation configuration at full size: N = 16,384,000 (FCC 160^3 x 4 at rho
+    0.70, displaced by up to 0.1, expanded by 1.05 to rho 0.6047), rc 3.0: forces of
+    200 sampled particles against direct all-pairs sums, FP32-force (the form the
+    cavitation run uses) and FP64."""
+    x, box = li.perturbed_fcc(16_384_000, 0.70, 0.1, 114)
+    x *= 1.05
+    box *= 1.05
+    rng = np.random.default_rng(115)
+    idx = rng.choice(len(x), size=200, replace=False)
+    xw = oracle.wrap(x, box)
+    ref = np.array([oracle.force_on(xw, box, 3.0, int(i)) for i in idx])
+    rms_ref = np.sqrt((ref ** 2).sum(1).mean())
+    for precision, tol in [(1, FP32_TOL), (0, FP64_TOL)]:
+        with make(ljmd, x, np.zeros_like(x), box, rc=3.0, precision=precision) as s:
+            f = s.forces()
+        assert np.abs(f[idx] - ref).max() / rms_ref <= tol
+
+
+def test_batched_configuration_forces(ljmd, oracle):
+    """The 256-replica configuration (N log-uniform in [500, 32000], rho and T
+    uniform) in one arena, after 50 steps (the initial lattices have net forces that
+    are small differences of large pair forces, below what FP32 pair arithmetic
+    resolves to 1e-5): forces of every eighth system at its current positions
+    against the oracle's, both precisions."""
+    syss = li.batch_systems(count=256, seed=1004)
+    for precision, tol in [(1, FP32_TOL), (0, FP64_TOL)]:
+        b = ljmd.LJBatch(systems=[(c.n, c.box, c.rc, c.skin) for c in syss], precision=precision)
+        try:
+            for k, c in enumerate(syss):
+                b.set_state(k, c.x, c.v)
+            b.step(50, [c.dt for c in syss])
+            for k in range(0, len(syss), 8):
+                c = syss[k]
+                xk, _ = b.get_state(k)
+                f = b.forces(k)
+                ref = oracle.forces(xk, c.box, c.rc)
+                assert force_err(f, ref) <= tol, k
+        finally:
+            b.close()
