@@ -62,6 +62,7 @@ class Request:
     rc: float = 2.5
     skin: float = 0.3
     dt: float = 0.005
+    cancel_after: float = math.nan  # seconds after arrival at which the client cancels
     # filled in by the server
     admitted: float = math.nan
     finished: float = math.nan
@@ -180,6 +181,28 @@ class MDServer:
                 r.active = on
         return active
 
+    def cancel(self, r: Request, now: float):
+        """Withdraw a request: drop it from the queue, or free its arena space if it
+        is running (the other runs are not affected)."""
+        if r in self.pending:
+            self.pending.remove(r)
+            fut = self.prepared.pop(id(r), None)
+            if fut is not None:
+                fut.cancel()
+        elif r.sid in self.running and self.running[r.sid] is r:
+            self.running.pop(r.sid)
+            self.batch.remove(r.sid)
+        else:
+            return
+        r.result = dict(cancelled=True)
+        r.finished = now
+        self.done.append(r)
+
+    def _cancel_due(self, now: float):
+        for r in [q for q in list(self.pending) + list(self.running.values())
+                  if not math.isnan(q.cancel_after) and q.arrival + q.cancel_after <= now]:
+            self.cancel(r, now)
+
     def step_chunk(self) -> int:
         if not self.running:
             return 0
@@ -229,6 +252,7 @@ class MDServer:
                     self.done.append(r)
                     continue
                 self.submit(r)
+            self._cancel_due(now)
             if self.pending:
                 self.admit(now)
             if self.running:
@@ -241,7 +265,7 @@ class MDServer:
         return self.summary(reqs, wall)
 
     def summary(self, reqs: list[Request], wall: float) -> dict:
-        done = [r for r in self.done if "rejected" not in r.result]
+        done = [r for r in self.done if "rejected" not in r.result and "cancelled" not in r.result]
         lat = np.array([r.finished - r.arrival for r in done]) if done else np.array([math.nan])
         wait = np.array([r.admitted - r.arrival for r in done]) if done else np.array([math.nan])
         done_ids = {id(r) for r in self.done}
@@ -251,6 +275,7 @@ class MDServer:
         rate = self.particle_steps / wall if wall > 0 else math.nan
         return dict(requests=len(reqs), completed=len(done),
                     rejected=sum(1 for r in self.done if "rejected" in r.result),
+                    cancelled=sum(1 for r in self.done if "cancelled" in r.result),
                     unfinished=len(left), wall_s=wall,
                     p50_latency_s=float(np.nanpercentile(lat, 50)),
                     p99_latency_s=float(np.nanpercentile(lat, 99)),

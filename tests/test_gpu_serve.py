@@ -52,3 +52,39 @@ def test_request_larger_than_arena_is_rejected(ljmd):
     finally:
         srv.close()
     assert s["rejected"] == 1 and s["completed"] == 0
+
+
+def test_cancelled_requests_free_their_space(ljmd):
+    """Clients cancel two runs (one soon after arrival, one later): neither
+    completes, their arena space returns, and every other run completes with the
+    result it has alone."""
+    from paper_1210_3450_gb300 import serve
+    reqs = [serve.Request(id=k, arrival=0.001 * k, n=1500 + 300 * k, rho=0.8, temperature=1.0,
+                          steps=400, seed=2000 + k) for k in range(6)]
+    reqs[1].cancel_after = 0.0
+    reqs[3].steps = 1_000_000          # still running when it is cancelled
+    reqs[3].cancel_after = 0.2
+    srv = serve.MDServer(3 * 3500 * 900, precision=ljmd.MD_FP32_FORCE, chunk=20)
+    try:
+        summary = srv.run(reqs)
+        assert srv.batch.usage()["systems_used"] == 0
+    finally:
+        srv.close()
+    assert summary["cancelled"] == 2 and summary["completed"] == 4
+    for r in srv.done:
+        if r.id in (1, 3):
+            assert r.result == {"cancelled": True}
+            continue
+        x0, v0 = serve.initial_state(r)
+        with ljmd.LJSystem(r.box, r.n, r.rc, r.skin, ljmd.MD_FP32_FORCE) as s:
+            s.set_state(x0, v0)
+            s.step(r.steps, r.dt)
+            o = s.observables()
+        assert r.result["pe"] == o["pe"] and r.result["ke"] == o["ke"]
+
+
+def test_zero_budget_is_refused(ljmd):
+    from paper_1210_3450_gb300 import serve
+    with pytest.raises(ljmd.MDError) as e:
+        serve.MDServer(0, precision=ljmd.MD_FP32_FORCE)
+    assert e.value.code == ljmd.MD_ERR_ARG
