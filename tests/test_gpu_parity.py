@@ -309,3 +309,30 @@ def test_batched_configuration_forces(ljmd, oracle):
                 assert force_err(f, ref) <= tol, k
         finally:
             b.close()
+
+
+def test_max_size_sampled_forces_and_steps(ljmd, oracle):
+    """The largest system the library takes, N = 2^26 - 1 = 67,108,863 (FCC 256^3 x 4 at
+    rho 0.8442 less one site, displaced by up to 0.1; the last tile holds 31
+    particles): FP32-force forces of 24 sampled particles, the last one among them,
+    against direct all-pairs sums; the list size; then 10 steps through the rebuild
+    machinery with finite observables. N + 1 is refused."""
+    n = ljmd.MD_MAX_N
+    x, box = li.perturbed_fcc(n, 0.8442, 0.1, 116)
+    rng = np.random.default_rng(117)
+    idx = np.concatenate([rng.choice(n - 1, size=23, replace=False), [n - 1]])
+    ref = np.array([oracle.force_on(x, box, 2.5, int(i)) for i in idx])
+    rms_ref = np.sqrt((ref ** 2).sum(1).mean())
+    with make(ljmd, x, np.zeros_like(x), box, precision=1) as s:
+        f = s.forces()
+        assert np.abs(f[idx] - ref).max() / rms_ref <= FP32_TOL
+        assert 70 * n < s.list_size() < 90 * n
+        del f
+        s.set_state(x, li.maxwell_boltzmann(n, 0.722, 118))
+        s.step(10, 0.005)
+        o = s.observables()
+        assert all(np.isfinite(val) for val in o.values())
+        assert s.stats()["steps"] == 10
+    with pytest.raises(ljmd.MDError) as e:
+        ljmd.LJSystem(box, n + 1, 2.5, 0.3)
+    assert e.value.code == ljmd.MD_ERR_ARG
