@@ -22,6 +22,10 @@ constexpr int kTile = 32;
 constexpr int kIdxBits = 26;
 constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 
+// Cells per chunk of the two-pass cell-count scan (256 threads x 4 cells).
+constexpr int kScanChunk = 1024;
+__host__ __device__ inline int32_t scan_chunks(int64_t ncell) { return (int32_t)((ncell + kScanChunk - 1) / kScanChunk); }
+
 // Word index of list entry k of the particle in lane `lane` of local tile tl
 // (kmax is a multiple of 8).
 __host__ __device__ inline int64_t list_word(int64_t l_off, int tl, int kmax, int lane, int k) {
@@ -127,6 +131,9 @@ struct DevArrays {
   const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
   const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
   const int32_t* reb_pref;    // exclusive prefix of the rebuilding systems' tile counts (nreb + 1)
+  int32_t* chunk_pref;        // exclusive prefix of the rebuilding systems' cell-chunk counts (nreb + 1)
+  int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems (scan scratch)
+  int32_t chunk_cap;          // entries of chunk_sum
   int32_t nreb;               // rebuilding systems (host-driven passes; the graph reads ctl->nreb)
   int32_t* tile_next;         // work counter of the list build (reset before each build)
   const int32_t* tile_sys;  // system of each global tile
@@ -148,7 +155,12 @@ struct Tuning {
 // All launches cover every tile of every active system; warps of inactive
 // systems (or of systems not rebuilding, for the rebuild kernels) return early.
 
+// Kernels of one rebuild pass: count, the two scan passes, scatter, rank, gather,
+// copy-back, list build.
+constexpr int kRebuildLaunches = 8;
+
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
+// Exclusive scan of the cell counts into the cell starts (two launches).
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
 void launch_scatter(const DevArrays& a, cudaStream_t s);
 void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s);

@@ -283,7 +283,7 @@ void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
-  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart);
+  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_); hfree(h_obs_work_);
@@ -364,6 +364,9 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.perm2, P));
   CKR(dmalloc(&d_.ccount, caps_.cells));
   CKR(dmalloc(&d_.cstart, caps_.cells));
+  // a system of ncell cells has at most ncell / kScanChunk + 1 chunks
+  d_.chunk_cap = (int32_t)(caps_.cells / kScanChunk + ns + 1);
+  CKR(dmalloc(&d_.chunk_sum, d_.chunk_cap));
   CK(cudaMemset(d_.v, 0, sizeof(double4_32a) * P));
   CK(cudaMemset(d_.f, 0, sizeof(double4_32a) * P));
   CK(cudaMemset(d_.xref, 0, sizeof(double4_32a) * P));
@@ -376,7 +379,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_disp2_, ns));
   CKR(dmalloc(&d_margin_, ns));
   CK(cudaMemset(d_margin_, 0, sizeof(double) * ns));
-  CKR(dmalloc(&d_rebuild_, 3 * ns + 1));
+  CKR(dmalloc(&d_rebuild_, 4 * ns + 2));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
   CKR(dmalloc(&d_obs_work_, 2 * ns + 1));
@@ -389,7 +392,7 @@ int Engine::alloc_arrays() {
   CK(cudaMemset(d_tile_sys_, 0xff, sizeof(int32_t) * T));
   CK(cudaMallocHost((void**)&h_status_, sizeof(SysStatus) * ns));
   CK(cudaMallocHost((void**)&h_disp2_, sizeof(unsigned long long) * ns));
-  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * (3 * ns + 1)));
+  CK(cudaMallocHost((void**)&h_rebuild_, sizeof(int32_t) * (4 * ns + 2)));
   CK(cudaMallocHost((void**)&h_obs_, sizeof(double) * 3 * ns));
   CKR(dmalloc(&d_ctl_, 1));
   CKR(dmalloc(&d_reb_count_, ns));
@@ -580,6 +583,7 @@ DevArrays Engine::arrays() const {
   a.rebuild = d_rebuild_;
   a.rebuild_ids = d_rebuild_ + nsys();
   a.reb_pref = d_rebuild_ + 2 * nsys();
+  a.chunk_pref = d_rebuild_ + 3 * nsys() + 1;
   a.nreb = 0;
   a.tile_next = &d_ctl_->next_tile;
   a.tile_sys = d_tile_sys_;
@@ -683,16 +687,20 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
   for (int attempt = 0; attempt < 4; ++attempt) {
     for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = 0;
     int32_t* pref = h_rebuild_ + 2 * nsys();
-    int32_t tiles = 0;
+    int32_t* cpref = h_rebuild_ + 3 * nsys() + 1;
+    int32_t tiles = 0, chunks = 0;
     for (size_t q = 0; q < which.size(); ++q) {
       h_rebuild_[which[q]] = 1;
       h_rebuild_[nsys() + q] = which[q];
       pref[q] = tiles;
+      cpref[q] = chunks;
       tiles += sys_[which[q]].ntiles;
+      chunks += scan_chunks(sys_[which[q]].ncell);
     }
     const int nreb = (int)which.size();
     pref[nreb] = tiles;
-    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (3 * nsys() + 1), cudaMemcpyHostToDevice, s));
+    cpref[nreb] = chunks;
+    CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (4 * nsys() + 2), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(d_status_, 0, sizeof(SysStatus) * nsys(), s));
     CK(cudaMemsetAsync(&d_ctl_->next_tile, 0, sizeof(int32_t), s));
     DevArrays a = arrays();
@@ -709,7 +717,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     launch_build_list(a, cur_, list_tuning(), s);
     tmark_end(s);
     CKL();
-    n_launch_ += 7;
+    n_launch_ += kRebuildLaunches;
     n_rebuild_seq_ += 1;
     CK(cudaMemcpyAsync(h_status_, d_status_, sizeof(SysStatus) * nsys(), cudaMemcpyDeviceToHost, s));
     CKR(sync_check(s));
@@ -981,7 +989,7 @@ int Engine::run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream
   const GraphCtl r = *h_ctl_;
   *done = r.done;
   if (r.done & 1) cur_ ^= 1;
-  n_launch_ += (half_ ? 3 : 2) * (int64_t)r.done + 7 * (int64_t)r.passes;
+  n_launch_ += (half_ ? 3 : 2) * (int64_t)r.done + kRebuildLaunches * (int64_t)r.passes;
   n_rebuild_seq_ += r.passes;
   for (int k = 0; k < nsys(); ++k) {
     if (h_reb_count_[k] <= 0) continue;

@@ -232,7 +232,7 @@ class Engine {
   SysStatus* d_status_ = nullptr;
   unsigned long long* d_disp2_ = nullptr;
   double* d_margin_ = nullptr;
-  int32_t* d_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
+  int32_t* d_rebuild_ = nullptr;  // flags (nsys), compact ids (nsys), tile prefix (nsys + 1), chunk prefix (nsys + 1)
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;
   int32_t* d_obs_work_ = nullptr;  // selected systems and their chunk prefix (observables)
@@ -244,7 +244,7 @@ class Engine {
   // pinned host mirrors
   SysStatus* h_status_ = nullptr;
   unsigned long long* h_disp2_ = nullptr;
-  int32_t* h_rebuild_ = nullptr;  // flags (nsys) followed by compact ids (nsys)
+  int32_t* h_rebuild_ = nullptr;  // the same layout as d_rebuild_
   double* h_obs_ = nullptr;
 };
 

@@ -159,65 +159,111 @@ __global__ void k_cell_count(DevArrays a, int cur) {
   });
 }
 
-// Exclusive scan of the cell counts of one rebuilding system per block (blocks
-// stride over the rebuilding systems). Each of the 32 warps owns a contiguous
-// segment of cells read 32 at a time (coalesced): pass 1 sums the segment, one
-// warp scans the 32 segment sums, pass 2 scans the segment with its offset and
-// writes the starts; the counts are reset to serve as fill counters of the
-// scatter.
-__global__ void __launch_bounds__(1024) k_cell_scan(DevArrays a, int nreb) {
+// Exclusive scan of the cell counts of the rebuilding systems, in two passes over
+// chunks of kScanChunk cells so that a large system spreads over many blocks:
+// k_cell_sums totals each chunk, k_cell_starts adds the totals of the system's
+// earlier chunks to a block scan of its own chunk and writes the starts. Work
+// item w is chunk w - chunk_pref[r] of rebuilding system r. The counts are reset
+// to serve as fill counters of the scatter.
+constexpr int kScanBlock = kScanChunk / 4;
+
+__device__ __forceinline__ int chunk_system(const DevArrays& a, int nreb, int w) {
+  int lo = 0, hi = nreb - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    if (a.chunk_pref[m] <= w) lo = m;
+    else hi = m - 1;
+  }
+  return lo;
+}
+
+// Sum over the block (every thread receives it); ws holds kScanBlock / 32 ints.
+__device__ __forceinline__ int block_sum(int v, int* ws) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = __reduce_add_sync(kFull, v);
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  int t = lane < kScanBlock / 32 ? ws[lane] : 0;
+  t = __reduce_add_sync(kFull, t);
+  __syncthreads();  // ws is reused by the caller's next block-wide step
+  return t;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_cell_sums(DevArrays a, int nreb) {
   if (a.ctl) nreb = a.ctl->nreb;  // graph-captured loop: the count is decided on the device
-  __shared__ int wsum[32];
-  __shared__ int total_s;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int r = blockIdx.x; r < nreb; r += gridDim.x) {
+  if (nreb <= 0) return;
+  __shared__ int ws[kScanBlock / 32];
+  const int total = a.chunk_pref[nreb];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int r = chunk_system(a, nreb, w);
     const int sys = a.rebuild_ids[r];
     const SysParams& P = a.params[sys];
     if (!P.active || !a.rebuild[sys]) continue;  // uniform over the block
     const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+    const int64_t c0 = (int64_t)(w - a.chunk_pref[r]) * kScanChunk + 4 * threadIdx.x;
+    const int32_t* cnt = a.ccount + P.c_off;
+    int part = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) part += c0 + m < ncell ? cnt[c0 + m] : 0;
+    part = block_sum(part, ws);
+    if (threadIdx.x == 0) a.chunk_sum[w] = part;
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nreb) {
+  if (a.ctl) nreb = a.ctl->nreb;
+  if (nreb <= 0) return;
+  __shared__ int ws[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int total = a.chunk_pref[nreb];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int r = chunk_system(a, nreb, w);
+    const int sys = a.rebuild_ids[r];
+    const SysParams& P = a.params[sys];
+    if (!P.active || !a.rebuild[sys]) continue;  // uniform over the block
+    const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
+    const int k = w - a.chunk_pref[r];
+    // particles in the system's earlier chunks
+    int off = 0;
+    for (int q = a.chunk_pref[r] + (int)threadIdx.x; q < w; q += kScanBlock) off += a.chunk_sum[q];
+    off = block_sum(off, ws);
     int32_t* cnt = a.ccount + P.c_off;
     int32_t* cst = a.cstart + P.c_off;
-    const int64_t seg = (ncell + 1023) / 1024 * 32;  // a multiple of 32
-    const int64_t s0 = min(ncell, (int64_t)w * seg), s1 = min(ncell, s0 + seg);
-    int part = 0;
-#pragma unroll 4
-    for (int64_t c = s0 + lane; c < s1; c += 32) part += cnt[c];
-    const int wtot = __reduce_add_sync(kFull, part);
-    if (lane == 0) wsum[w] = wtot;
-    __syncthreads();
-    if (w == 0) {
-      const int ws = wsum[lane];
-      int wi = ws;
+    const int64_t c0 = (int64_t)k * kScanChunk + 4 * threadIdx.x;
+    int v[4];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, wi, o);
-        if (lane >= o) wi += y;
-      }
-      wsum[lane] = wi - ws;
-      if (lane == 31) total_s = wi;
-    }
-    __syncthreads();
-    int carry = wsum[w];
-    for (int64_t b = s0; b < s1; b += 32) {
-      const int64_t c = b + lane;
-      const int v = c < s1 ? cnt[c] : 0;
-      int incl = v;
+    for (int m = 0; m < 4; ++m) v[m] = c0 + m < ncell ? cnt[c0 + m] : 0;
+    const int tsum = v[0] + v[1] + v[2] + v[3];
+    // exclusive scan of tsum over the block
+    int incl = tsum;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (c < s1) {
-        cst[c] = carry + incl - v;
-        cnt[c] = 0;
-      }
-      carry += __shfl_sync(kFull, incl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (tid == 0) {
-      cst[ncell] = total_s;
-      a.margin[sys] = P.skin;  // velocity-bound rule: a fresh list has the whole skin
+    if (lane == 31) ws[wi] = incl;
+    __syncthreads();
+    int wpre = 0, btot = 0;
+#pragma unroll
+    for (int q = 0; q < kScanBlock / 32; ++q) {
+      const int t = ws[q];
+      wpre += q < wi ? t : 0;
+      btot += t;
     }
-    __syncthreads();  // wsum and total_s are reused by the next system
+    int run = off + wpre + incl - tsum;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (c0 + m < ncell) {
+        cst[c0 + m] = run;
+        cnt[c0 + m] = 0;
+      }
+      run += v[m];
+    }
+    if (threadIdx.x == 0) {
+      if ((int64_t)(k + 1) * kScanChunk >= ncell) cst[ncell] = off + btot;  // the system's last chunk
+      if (k == 0) a.margin[sys] = P.skin;  // velocity-bound rule: a fresh list has the whole skin
+    }
+    __syncthreads();  // ws is reused by the next chunk
   }
 }
 
@@ -1398,7 +1444,10 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     return;
   }
   __shared__ int wsum[32];
+  __shared__ long long wsum64[32];
   __shared__ int base_s, bad_s, total_s;
+  __shared__ long long total64_s;
+  int32_t* chunk_pref = a.chunk_pref;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) { base_s = 0; bad_s = 0; }
   __syncthreads();
@@ -1413,7 +1462,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
         if (a.status[k].nonfinite) bad_s = 1;
         if (P.rule == 1) {
           // velocity bound (DUTC): the margin shrinks by 2 v_max dt per step; a
-          // rebuild restores it (k_cell_scan)
+          // rebuild restores it (k_cell_starts)
           const double m =
               __dsub_rn(a.margin[k],
                         __dmul_rn(__dmul_rn(2.0, __dsqrt_rn(__longlong_as_double((long long)d2))), P.dt));
@@ -1452,39 +1501,50 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     if (threadIdx.x == 0) base_s += total_s;
     __syncthreads();
   }
-  // prefix of the rebuilding systems' tile counts (the rebuild kernels' work list)
+  // prefixes of the rebuilding systems' tile counts (the rebuild kernels' work
+  // list) and of their cell-chunk counts (the cell scan's work list), as one
+  // scan of the pair packed in 64 bits
   const int nreb_all = base_s;
-  int carry = 0;
+  long long carry = 0;
   for (int r0 = 0; r0 < nreb_all; r0 += (int)blockDim.x) {
     const int r = r0 + (int)threadIdx.x;
-    const int v = r < nreb_all ? a.params[rebuild_ids[r]].ntiles : 0;
-    int incl = v;
+    long long v = 0;
+    if (r < nreb_all) {
+      const SysParams& P = a.params[rebuild_ids[r]];
+      v = ((long long)scan_chunks((int64_t)P.nc * P.nc * P.nc) << 32) | (unsigned)P.ntiles;
+    }
+    long long incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o);
+      const long long y = __shfl_up_sync(kFull, incl, o);
       if (lane >= o) incl += y;
     }
-    if (lane == 31) wsum[w] = incl;
+    if (lane == 31) wsum64[w] = incl;
     __syncthreads();
     if (w == 0) {
-      const int ws = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-      int wi = ws;
+      const long long ws = lane < (int)(blockDim.x >> 5) ? wsum64[lane] : 0;
+      long long wi = ws;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, wi, o);
+        const long long y = __shfl_up_sync(kFull, wi, o);
         if (lane >= o) wi += y;
       }
-      wsum[lane] = wi - ws;
-      if (lane == 31) total_s = wi;
+      wsum64[lane] = wi - ws;
+      if (lane == 31) total64_s = wi;
     }
     __syncthreads();
-    if (r < nreb_all) reb_pref[r] = carry + wsum[w] + incl - v;
-    carry += total_s;
+    if (r < nreb_all) {
+      const long long e = carry + wsum64[w] + incl - v;
+      reb_pref[r] = (int32_t)(e & 0xffffffffll);
+      chunk_pref[r] = (int32_t)(e >> 32);
+    }
+    carry += total64_s;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     const int nreb = base_s;
-    reb_pref[nreb] = carry;
+    reb_pref[nreb] = (int32_t)(carry & 0xffffffffll);
+    chunk_pref[nreb] = (int32_t)(carry >> 32);
     *a.tile_next = 0;
     c->done += 1;
     if (bad_s) {
@@ -1524,7 +1584,10 @@ void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
   k_cell_count<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
-  k_cell_scan<<<(unsigned)std::min(std::max(nreb, 1), 1024), 1024, 0, s>>>(a, nreb);
+  // blocks stride over the chunks: one wave of 8 blocks per SM at most
+  const unsigned g = (unsigned)std::max(1, std::min(a.chunk_cap, 152 * 8));
+  k_cell_sums<<<g, kScanBlock, 0, s>>>(a, nreb);
+  k_cell_starts<<<g, kScanBlock, 0, s>>>(a, nreb);
 }
 void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<bin_blocks(a), kBlock, 0, s>>>(a); }
 void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s) {
