@@ -114,7 +114,7 @@ struct DevArrays {
   uint32_t* nbr;      // list words
   double* tile_obs;   // per-tile (PE, W, KE) partial sums for observables
   // rebuild scratch
-  double4_32a* xtmp;
+  long long* skey;    // sort key (x bits) of each scattered position
   double4_32a* vtmp;
   float4* xf;         // positions as float at the last list build (list pre-test; 4 spare entries)
   int32_t* idtmp;
@@ -162,8 +162,8 @@ constexpr int kRebuildLaunches = 8;
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
 // Exclusive scan of the cell counts into the cell starts (two launches).
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
-void launch_scatter(const DevArrays& a, cudaStream_t s);
-void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s);
+void launch_scatter(const DevArrays& a, int cur, cudaStream_t s);
+void launch_cell_rank(const DevArrays& a, cudaStream_t s);
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);

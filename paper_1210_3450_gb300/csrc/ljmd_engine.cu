@@ -282,7 +282,7 @@ int footprint(const SysSpec& s, SysFootprint* f, SysHost* h) {
 void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
-  dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.xtmp); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
+  dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.skey); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
@@ -354,7 +354,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.ncnt, P));
   CKR(dmalloc(&d_.nbr, caps_.list_words));
   CKR(dmalloc(&d_.tile_obs, 3 * T));
-  CKR(dmalloc(&d_.xtmp, P));
+  CKR(dmalloc(&d_.skey, P));
   CKR(dmalloc(&d_.xf, P + 4));
   CK(cudaMemset(d_.xf, 0, sizeof(float4) * (P + 4)));
   CKR(dmalloc(&d_.vtmp, P));
@@ -708,8 +708,8 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     tmark_begin(kTBin, s);
     launch_cell_count(a, cur_, s);
     launch_cell_scan(a, nreb, s);
-    launch_scatter(a, s);
-    launch_cell_rank(a, cur_, s);
+    launch_scatter(a, cur_, s);
+    launch_cell_rank(a, s);
     launch_gather(a, cur_, s);
     launch_copyback(a, cur_, s);
     tmark_end(s);
@@ -922,8 +922,8 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
       const int c1 = c ^ 1;
       launch_cell_count(a, c1, cap_[1]);
       launch_cell_scan(a, nused, cap_[1]);
-      launch_scatter(a, cap_[1]);
-      launch_cell_rank(a, c1, cap_[1]);
+      launch_scatter(a, c1, cap_[1]);
+      launch_cell_rank(a, cap_[1]);
       launch_gather(a, c1, cap_[1]);
       launch_copyback(a, c1, cap_[1]);
       launch_build_list(a, c1, list_tuning(), cap_[1]);

@@ -267,7 +267,12 @@ __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nre
   }
 }
 
-__global__ void k_scatter(DevArrays a) {
+// Scatter into cell order (arbitrary within a cell). Beside the old slot, the
+// scattered position receives the particle's sort key (x, then caller index) and
+// cell, so that the ranking below reads them contiguously (the id and cell go to
+// the gather's scratch arrays, unused until the gather).
+
+__global__ void k_scatter(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
     if (P.nc == 1) {
@@ -276,7 +281,12 @@ __global__ void k_scatter(DevArrays a) {
     }
     const int c = a.cell[t.s];
     const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
-    a.perm[P.p_off + pos] = t.local;
+    const int64_t d = P.p_off + pos;
+    a.perm[d] = t.local;
+    // x >= 0 (wrapped at the count), so its bit pattern orders like the value
+    a.skey[d] = __double_as_longlong(a.x[cur][t.s].x);
+    a.idtmp[d] = a.id[t.s];
+    a.celltmp[d] = c;
   });
 }
 
@@ -284,41 +294,47 @@ __global__ void k_scatter(DevArrays a) {
 // A row of neighbouring cells along x is then sorted by x as a whole, which lets
 // the list build restrict each row to the window |x_j - x_i| < rl. One thread per
 // particle: its place in the cell is the number of the cell's particles with a
-// smaller key (x bits, then caller index), counted over the scattered members.
-// The first member of each cell resets the cell's fill counter.
-__global__ void k_cell_rank(DevArrays a, int cur) {
+// smaller key, counted over the scattered members. The first member of each cell
+// resets the cell's fill counter.
+__global__ void k_cell_rank(DevArrays a) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
-    const int32_t* pm = a.perm + P.p_off;
-    const int p = t.local;  // position in the scattered order
-    const int i = pm[p];    // the particle's slot before the rebuild
+    const int p = t.local;           // position in the scattered order
+    const int i = a.perm[t.s];       // the particle's slot before the rebuild
     if (P.nc == 1) {
       a.perm2[t.s] = i;
       return;
     }
-    const int c = a.cell[P.p_off + i];
+    const long long* key = a.skey + P.p_off;
+    const int32_t* idk = a.idtmp + P.p_off;
+    const int c = a.celltmp[t.s];
     const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
     if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
-    const double4_32a* xs = a.x[cur] + P.p_off;
-    const int32_t* id = a.id + P.p_off;
-    // keys: x >= 0 (wrapped), so its bit pattern orders like the value
-    const long long ki = __double_as_longlong(xs[i].x);
-    const int32_t idi = id[i];
+    const long long ki = key[p];
+    const int32_t idi = idk[p];
     int rank = 0;
     for (int q = lo; q < hi; ++q) {
-      const int j = pm[q];
-      const long long kj = __double_as_longlong(xs[j].x);
-      rank += (kj < ki || (kj == ki && id[j] < idi)) ? 1 : 0;
+      const long long kj = key[q];
+      rank += (kj < ki || (kj == ki && idk[q] < idi)) ? 1 : 0;
     }
     a.perm2[P.p_off + lo + rank] = i;
   });
 }
 
+// Gather into the sorted order. The positions go straight to the arrays that
+// only the new order uses (the build-time positions and their shadows); the
+// velocities, ids and cells go through scratch and are copied back.
 __global__ void k_gather(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
     const int64_t old = P.p_off + a.perm2[t.s];
-    a.xtmp[t.s] = a.x[cur][old];
+    const double4_32a x = a.x[cur][old];
+    a.xref[t.s] = x;
+    int4 q = fixed4(x, P.qscale);
+    a.xqref[t.s] = q;
+    q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
+    a.xq[cur][t.s] = q;
+    a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
     a.vtmp[t.s] = a.v[old];
     a.idtmp[t.s] = a.id[old];
     a.celltmp[t.s] = a.cell[old];
@@ -328,14 +344,7 @@ __global__ void k_gather(DevArrays a, int cur) {
 __global__ void k_copyback(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
-    const double4_32a x = a.xtmp[t.s];
-    a.x[cur][t.s] = x;
-    a.xref[t.s] = x;
-    int4 q = fixed4(x, P.qscale);
-    a.xqref[t.s] = q;
-    q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
-    a.xq[cur][t.s] = q;
-    a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
+    a.x[cur][t.s] = a.xref[t.s];
     a.v[t.s] = a.vtmp[t.s];
     a.id[t.s] = a.idtmp[t.s];
     a.cell[t.s] = a.celltmp[t.s];
@@ -1589,10 +1598,10 @@ void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
   k_cell_sums<<<g, kScanBlock, 0, s>>>(a, nreb);
   k_cell_starts<<<g, kScanBlock, 0, s>>>(a, nreb);
 }
-void launch_scatter(const DevArrays& a, cudaStream_t s) { k_scatter<<<bin_blocks(a), kBlock, 0, s>>>(a); }
-void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s) {
-  k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
+void launch_scatter(const DevArrays& a, int cur, cudaStream_t s) {
+  k_scatter<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
+void launch_cell_rank(const DevArrays& a, cudaStream_t s) { k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a); }
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<bin_blocks(a), kBlock, 0, s>>>(a, cur); }
 void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
   k_copyback<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);

@@ -36,7 +36,7 @@ from . import ljmd  # noqa: E402
 # Device bytes per particle slot of the arena (positions x2, velocity, two
 # reference copies, forces, half-list force sums, shadow positions x2, float
 # positions for the list build, indices and rebuild scratch).
-SLOT_BYTES = 348
+SLOT_BYTES = 324
 LIST_WORD_BYTES = 4
 CELL_BYTES = 8
 
