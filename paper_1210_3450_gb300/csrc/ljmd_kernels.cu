@@ -1222,8 +1222,12 @@ __global__ void __launch_bounds__(kBlock) k_integrate_half(DevArrays a, int cur,
 
 // Per particle: 1/2 sum_j V(r) and 1/2 sum_j -r V'(r) over listed partners with
 // r < rc (the full list counts each pair twice; a half list once, without the
-// 1/2), and 1/2 |v|^2; each tile sums
-// its 32 values in a fixed shuffle order into tile_obs[3 t ...].
+// 1/2), and 1/2 |v|^2; each tile sums its 32 values in a fixed shuffle order into
+// tile_obs[3 t ...]. With V(r) = 4 (r^-12 - r^-6) + 4 c2 r^2 + 4 c0 (Eq. 1) and
+// -r V'(r) = 48 r^-12 - 24 r^-6 - 8 c2 r^2, the pair loop only sums r^-12, r^-6
+// and r^2 and counts the pairs inside rc: 9 FP64 operations per pair inside rc
+// and 6 per listed pair (the periodic image is added only where the list word
+// names one; the cutoff and range tests compare bit patterns, r^2 >= 0).
 __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs,
                                                       const int32_t* __restrict__ select) {
   TileCtx t;
@@ -1237,23 +1241,37 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
     const double4_32a* xs = a.x[cur] + P.p_off;
     const int cnt = a.ncnt[t.s];
     const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+    const long long rc2b = __double_as_longlong(P.rc2);
+    const long long tinyb = __double_as_longlong(1e-30);
+    const double L = P.L;
+    double s12 = 0.0, s6 = 0.0, sr = 0.0;
+    int nin = 0;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = lp[(int64_t)(k >> 2) * (4 * kTile) + (k & 3)];
+      const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
       const double4_32a xj = xs[e & kIdxMask];
+      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
       const unsigned code = e >> kIdxBits;
-      const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
-      const double dy = apply_image(xj.y - xi.y, (code >> 2) & 3u, P.L);
-      const double dz = apply_image(xj.z - xi.z, (code >> 4) & 3u, P.L);
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < P.rc2) {
+      if (code) {
+        dx = apply_image(dx, code & 3u, L);
+        dy = apply_image(dy, (code >> 2) & 3u, L);
+        dz = apply_image(dz, (code >> 4) & 3u, L);
+      }
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      const long long r2b = __double_as_longlong(r2);
+      if (r2b < rc2b) {
         // reciprocal within rounding in 3 DFMA (see rcp_f64); IEEE division only for
         // (near-)coincident pairs, outside rcp_f64's range
-        const double ir2 = r2 > 1e-30 ? rcp_f64(r2) : 1.0 / r2;
+        const double ir2 = r2b > tinyb ? rcp_f64(r2) : 1.0 / r2;
         const double ir6 = ir2 * ir2 * ir2;
-        pe += 4.0 * (ir6 * ir6 - ir6 + P.c2 * r2 + P.c0);
-        w += 48.0 * ir6 * ir6 - 24.0 * ir6 - 8.0 * P.c2 * r2;
+        s12 = fma(ir6, ir6, s12);
+        s6 += ir6;
+        sr += r2;
+        ++nin;
       }
     }
+    const double c2 = P.c2;
+    pe = 4.0 * (s12 - s6) + 4.0 * fma(c2, sr, P.c0 * (double)nin);
+    w = 48.0 * s12 - 24.0 * s6 - 8.0 * c2 * sr;
     if (!P.half) {  // the full list counts each pair twice
       pe *= 0.5;
       w *= 0.5;

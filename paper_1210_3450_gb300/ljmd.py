@@ -157,6 +157,18 @@ def _host3(a, n: int) -> np.ndarray:
     return a
 
 
+def _out3(out, n: int):
+    """Caller-provided (x, v) output arrays (C-contiguous float64, n x 3), or new ones."""
+    if out is None:
+        return np.empty((n, 3)), np.empty((n, 3))
+    x, v = out
+    for a in (x, v):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.shape == (n, 3)):
+            raise ValueError(f"output arrays must be C-contiguous float64 of shape ({n}, 3)")
+    return x, v
+
+
 def _pd(a: np.ndarray):
     return a.ctypes.data_as(_PD)
 
@@ -241,9 +253,10 @@ class LJSystem:
     def set_state_dev(self, x, v, stream=None):
         _check(_lib.md_set_state_dev(self._h, _dev_ptr(x, self.n), _dev_ptr(v, self.n), _stream_ptr(stream)))
 
-    def get_state(self):
-        x = np.empty((self.n, 3))
-        v = np.empty((self.n, 3))
+    def get_state(self, out=None):
+        """Positions (wrapped into [0, L)) and velocities in caller order; `out`
+        may give the (x, v) arrays to fill, e.g. views of pinned host memory."""
+        x, v = _out3(out, self.n)
         _check(_lib.md_get_state(self._h, _pd(x), _pd(v)))
         return x, v
 
@@ -459,10 +472,8 @@ class LJBatch:
         _check(_lib.md_batch_set_state_dev(self._h, int(sid), _dev_ptr(x, n), _dev_ptr(v, n),
                                            _stream_ptr(stream)))
 
-    def get_state(self, sid: int):
-        n = self._n[sid]
-        x = np.empty((n, 3))
-        v = np.empty((n, 3))
+    def get_state(self, sid: int, out=None):
+        x, v = _out3(out, self._n[sid])
         _check(_lib.md_batch_get_state(self._h, int(sid), _pd(x), _pd(v)))
         return x, v
 
