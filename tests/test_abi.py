@@ -58,3 +58,17 @@ def test_product_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\bimport oracle|from oracle|ljmd_oracle", text), f
+
+
+def test_state_output_arrays_are_checked(ljmd):
+    """get_state(out=...) takes caller arrays (e.g. views of pinned host memory) only
+    if they are C-contiguous float64 of shape (N, 3)."""
+    import numpy as np
+    x, v = ljmd._out3(None, 5)
+    assert x.shape == v.shape == (5, 3) and x.dtype == np.float64
+    good = (np.zeros((5, 3)), np.zeros((5, 3)))
+    assert ljmd._out3(good, 5)[0] is good[0]
+    for bad in [(np.zeros((5, 3), np.float32), good[1]), (good[0], np.zeros((4, 3))),
+                (np.zeros((3, 5)).T, good[1])]:
+        with pytest.raises(ValueError):
+            ljmd._out3(bad, 5)

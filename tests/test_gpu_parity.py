@@ -179,6 +179,23 @@ def test_trajectory_200_steps_fp64(ljmd, oracle):
     assert og["pe"] == pytest.approx(ro["pe"], rel=1e-10)
 
 
+def test_state_into_caller_arrays(ljmd):
+    """get_state(out=(x, v)) fills pinned host arrays with the same values as
+    get_state()."""
+    import torch
+    x, box = li.perturbed_fcc(4001, 0.8442, 0.1, 119)
+    v = li.maxwell_boltzmann(4001, 0.722, 120)
+    with make(ljmd, x, v, box, precision=1) as s:
+        s.step(25, 0.005)
+        x1, v1 = s.get_state()
+        xo = torch.empty((4001, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vo = torch.empty((4001, 3), dtype=torch.float64, pin_memory=True).numpy()
+        x2, v2 = s.get_state(out=(xo, vo))
+        assert x2 is xo and v2 is vo
+        np.testing.assert_array_equal(xo, x1)
+        np.testing.assert_array_equal(vo, v1)
+
+
 def test_split_steps_equal_one_call(ljmd):
     """md_step(100) equals md_step(40) + md_step(60) bit for bit (forces kept
     between calls, same rebuild points)."""
