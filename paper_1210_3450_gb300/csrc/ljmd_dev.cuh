@@ -156,8 +156,8 @@ struct Tuning {
 // systems (or of systems not rebuilding, for the rebuild kernels) return early.
 
 // Kernels of one rebuild pass: count, the two scan passes, scatter, rank, gather,
-// copy-back, list build.
-constexpr int kRebuildLaunches = 8;
+// list build (which also copies the gathered state back into place).
+constexpr int kRebuildLaunches = 7;
 
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
 // Exclusive scan of the cell counts into the cell starts (two launches).
@@ -165,7 +165,6 @@ void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
 void launch_scatter(const DevArrays& a, int cur, cudaStream_t s);
 void launch_cell_rank(const DevArrays& a, cudaStream_t s);
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
-void launch_copyback(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
 // Device-side list-validity decision of the graph-captured loop (see GraphCtl).
 // reb_count NULL: outside a graph (no step or pass counting, no node conditions).

@@ -711,7 +711,6 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     launch_scatter(a, cur_, s);
     launch_cell_rank(a, s);
     launch_gather(a, cur_, s);
-    launch_copyback(a, cur_, s);
     tmark_end(s);
     tmark_begin(kTList, s);
     launch_build_list(a, cur_, list_tuning(), s);
@@ -925,7 +924,6 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
       launch_scatter(a, c1, cap_[1]);
       launch_cell_rank(a, cap_[1]);
       launch_gather(a, c1, cap_[1]);
-      launch_copyback(a, c1, cap_[1]);
       launch_build_list(a, c1, list_tuning(), cap_[1]);
       cudaGraph_t t1 = nullptr;
       e = cudaStreamEndCapture(cap_[1], &t1);

@@ -323,7 +323,8 @@ __global__ void k_cell_rank(DevArrays a) {
 
 // Gather into the sorted order. The positions go straight to the arrays that
 // only the new order uses (the build-time positions and their shadows); the
-// velocities, ids and cells go through scratch and are copied back.
+// velocities, ids and cells go to scratch, and the list build copies them (and
+// the positions) back slot by slot (copy_back_slot).
 __global__ void k_gather(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
@@ -341,14 +342,14 @@ __global__ void k_gather(DevArrays a, int cur) {
   });
 }
 
-__global__ void k_copyback(DevArrays a, int cur) {
-  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
-    if (!t.act) return;
-    a.x[cur][t.s] = a.xref[t.s];
-    a.v[t.s] = a.vtmp[t.s];
-    a.id[t.s] = a.idtmp[t.s];
-    a.cell[t.s] = a.celltmp[t.s];
-  });
+// The rebuilt state of one slot back into place. The list build does this for the
+// tiles it builds: it reads only the build-time positions, shadows and scratch
+// cells, which the copy does not touch, so the copy needs no launch of its own.
+__device__ __forceinline__ void copy_back_slot(const DevArrays& a, int cur, int64_t s) {
+  a.x[cur][s] = a.xref[s];
+  a.v[s] = a.vtmp[s];
+  a.id[s] = a.idtmp[s];
+  a.cell[s] = a.celltmp[s];
 }
 
 // ----------------------------------------------- pair list (Sec. 2.1, Fig. 1)
@@ -380,7 +381,7 @@ __device__ __forceinline__ unsigned exact_inside(double xi, double yi, double zi
 // rl^2 are not kept in registers: the rare exact tests reload them.
 struct ListCtx {
   const SysParams* Pp;
-  const double4_32a* xs;  // FP64 positions of the system
+  const double4_32a* xs;  // FP64 positions of the system (build-time copy)
   uint32_t* out;          // the particle's list words
   int li;                 // the particle's slot in the system
   int count;
@@ -573,7 +574,7 @@ __device__ __forceinline__ void lane_rows(const DevArrays& a, int cur, const Sys
     T.hi2 = Pp->rl2q_hi;
   }
   const int32_t* cst = a.cstart + Pp->c_off;
-  const int ci = a.cell[p_off + li];
+  const int ci = a.celltmp[p_off + li];
   const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
   const int nparts = (cx == 0 || cx == nc - 1) ? 2 : 1;
   const double L = Pp->L;
@@ -682,7 +683,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
     const bool act = li < n;
     const int64_t p_off = Pp->p_off;
     const int kmax = Pp->kmax;
-    ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
+    ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
+    if (act) copy_back_slot(a, cur, p_off + li);
     if (act) {
       if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
       else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
@@ -714,7 +716,8 @@ __device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int
   const unsigned actm = __ballot_sync(kFull, act);
   const int64_t p_off = Pp->p_off;
   const int kmax = Pp->kmax;
-  ListCtx o{Pp, a.x[cur] + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, false};
+  ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, false};
+  if (act) copy_back_slot(a, cur, p_off + li);
   const int nc = Pp->nc;
   if (nc == 1) {
     if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
@@ -729,7 +732,7 @@ __device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int
   int cx = 0, rkey = -1;
   float xk = 0.f;
   if (act) {
-    const int ci = a.cell[p_off + li];
+    const int ci = a.celltmp[p_off + li];
     cx = ci % nc;
     rkey = ci / nc;  // row of cells (y, z)
     xk = xf[li].x;
@@ -1621,9 +1624,6 @@ void launch_scatter(const DevArrays& a, int cur, cudaStream_t s) {
 }
 void launch_cell_rank(const DevArrays& a, cudaStream_t s) { k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a); }
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<bin_blocks(a), kBlock, 0, s>>>(a, cur); }
-void launch_copyback(const DevArrays& a, int cur, cudaStream_t s) {
-  k_copyback<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
-}
 namespace {
 inline unsigned blocks_of(const DevArrays& a, int block) {
   return (unsigned)(((int64_t)a.ntiles * kTile + block - 1) / block);
