@@ -54,6 +54,7 @@ extern "C" {
 #define MD_ERR_TIMEOUT (-5)       /* a bounded device wait gave up                 */
 #define MD_ERR_CUDA (-6)          /* a CUDA runtime call failed                    */
 #define MD_ERR_STATE (-7)         /* call needs a state set by md_set_state first  */
+#define MD_ERR_CHECK (-8)         /* a device bounds check failed (checked build)   */
 
 /* Force precision modes (md_set_precision). */
 #define MD_FP64 0       /* all pair arithmetic in FP64                                   */
@@ -195,6 +196,14 @@ MD_API int md_get_cells(md_ctx* ctx, int32_t* cell, int32_t* nc_out);
 
 /* Number of entries of the current full pair list (sum of all list lengths). */
 MD_API int md_list_size(md_ctx* ctx, int64_t* total);
+
+/* Checked build only (see md_version): overwrite entry `entry` of the list of the
+ * particle in sorted slot `slot` with the raw 32-bit list word `word` (partner slot
+ * in bits 0..25, periodic image in bits 26..31), so that a test can show the device
+ * checks at work: a pair loop that meets an out-of-range partner records it, skips
+ * the partner, and the call returns MD_ERR_CHECK. The list is built first if
+ * needed. The product build returns MD_ERR_ARG. */
+MD_API int md_debug_set_list_word(md_ctx* ctx, int64_t slot, int32_t entry, uint32_t word);
 
 /* Current full list in caller numbering: start[N+1] (int64) and partners[total] (int32)
  * in the library's internal order per particle (sort to compare as sets). */
@@ -382,7 +391,14 @@ MD_API void md_batch_destroy(md_batch* b);
 /* Thread-local description of the last error on this thread ("" if none). */
 MD_API const char* md_last_error(void);
 
-/* Library version string. */
+/* Library version string; it ends in ", checked)" for the checked build.
+ *
+ * Checked build: the same sources compiled with LJMD_CHECKS. Its kernels verify
+ * their indices (cell of a particle, scatter and rank positions within a cell,
+ * gather sources, every partner slot the list build appends and every partner slot
+ * and list length a pair loop reads). A failed check is recorded in a per-system
+ * word and the access is skipped or clamped; the next call that synchronises returns
+ * MD_ERR_CHECK, and so does every later one. The product build has no checks. */
 MD_API const char* md_version(void);
 
 #ifdef __cplusplus

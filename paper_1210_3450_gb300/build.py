@@ -35,19 +35,24 @@ def _deps() -> list[str]:
     return out
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link if any source is newer than the library; return its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link if any source is newer than the library; return its path.
+    checked=True builds the variant with device bounds checks (LJMD_CHECKS) into
+    _build/checked/libljmd.so."""
+    out_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
+    lib = os.path.join(out_dir, "libljmd.so")
+    flags = NVCC_FLAGS + (["-DLJMD_CHECKS"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
+    if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(p) for p in _deps())
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
+        if os.path.getmtime(lib) >= newest:
+            return lib
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
+        cmd = [nvcc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,14 +62,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False, verbose: bool = False) -> list[str]:
+    """The product library and the checked variant, compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = [ex.submit(build, force, verbose, c) for c in (False, True)]
+        return [f.result() for f in futs]
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build_all(force="--force" in sys.argv, verbose=True))

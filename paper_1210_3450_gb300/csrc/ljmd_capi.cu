@@ -297,6 +297,12 @@ int md_list_size(md_ctx* c, int64_t* total) {
   return c->eng.list_size(0, total, c->stream);
 }
 
+int md_debug_set_list_word(md_ctx* c, int64_t slot, int32_t entry, uint32_t word) {
+  int r = check_ctx(c);
+  if (r) return r;
+  return c->eng.debug_set_list_word(0, slot, entry, word, c->stream);
+}
+
 int md_get_list(md_ctx* c, int64_t* start, int32_t* partners) {
   int r = check_ctx(c);
   if (r) return r;
@@ -755,6 +761,12 @@ void md_batch_destroy(md_batch* b) {
   if (s) cudaStreamDestroy(s);
 }
 
-const char* md_version(void) { return "ljmd 0.1 (sm_103a)"; }
+const char* md_version(void) {
+#ifdef LJMD_CHECKS
+  return "ljmd 0.1 (sm_103a, checked)";
+#else
+  return "ljmd 0.1 (sm_103a)";
+#endif
+}
 
 }  // extern "C"

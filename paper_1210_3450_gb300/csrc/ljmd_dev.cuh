@@ -136,10 +136,34 @@ struct DevArrays {
   int32_t chunk_cap;          // entries of chunk_sum
   int32_t nreb;               // rebuilding systems (host-driven passes; the graph reads ctl->nreb)
   int32_t* tile_next;         // work counter of the list build (reset before each build)
+  int32_t* checks;            // per system: failed device checks (bits of CheckBits; checked build)
   const int32_t* tile_sys;  // system of each global tile
   int32_t ntiles;
   GraphCtl* ctl;            // graph-captured loop: step flags, rebuild count, abort word
 };
+
+// Device bounds checks of the checked build (compiled with LJMD_CHECKS): a failed
+// check sets a bit of the system's check word, the access is skipped or clamped to
+// a valid one, and the host reports MD_ERR_CHECK at its next synchronisation. The
+// product build compiles them out (check_ok is constant true).
+#ifdef LJMD_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+enum CheckBits : int {
+  kChkCell = 1,       // binning: cell index outside [0, ncell)
+  kChkScatter = 2,    // scatter: position past the end of the particle's cell
+  kChkRank = 4,       // in-cell ranking: position past the end of the cell
+  kChkGather = 8,     // gather: source slot outside [0, n)
+  kChkListEntry = 16, // list build: partner slot outside [0, n), or the particle itself
+  kChkPartner = 32,   // pair loops: listed partner slot outside [0, n)
+  kChkCount = 64,     // pair loops: list length above the capacity kmax
+};
+__device__ __forceinline__ bool check_ok(const DevArrays& a, int sys, bool ok, int bit) {
+  if (kChecks && !ok) atomicOr(&a.checks[sys], bit);
+  return !kChecks || ok;
+}
 
 // Launch shapes of the hot kernels (threads per block; partner groups of four
 // per FP32 iteration), chosen by the autotuner.

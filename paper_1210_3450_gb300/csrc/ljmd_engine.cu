@@ -284,7 +284,7 @@ void Engine::free_all() {
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.skey); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
-  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_rebuild_); dfree(d_tile_sys_);
+  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_checks_); dfree(d_rebuild_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_); hfree(h_obs_work_);
   drop_graphs();
@@ -379,6 +379,8 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_disp2_, ns));
   CKR(dmalloc(&d_margin_, ns));
   CK(cudaMemset(d_margin_, 0, sizeof(double) * ns));
+  CKR(dmalloc(&d_checks_, ns));
+  CK(cudaMemset(d_checks_, 0, sizeof(int32_t) * ns));
   CKR(dmalloc(&d_rebuild_, 4 * ns + 2));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
@@ -580,6 +582,7 @@ DevArrays Engine::arrays() const {
   a.status = d_status_;
   a.disp2 = d_disp2_;
   a.margin = d_margin_;
+  a.checks = d_checks_;
   a.rebuild = d_rebuild_;
   a.rebuild_ids = d_rebuild_ + nsys();
   a.reb_pref = d_rebuild_ + 2 * nsys();
@@ -678,6 +681,23 @@ int Engine::get_state_dev(int k, double* x, double* v, cudaStream_t s) {
 int Engine::sync_check(cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   collect_timing();
+  if (kChecks) return read_checks(s);
+  return kOK;
+}
+
+// The device check words stay set once a check has failed (the state is suspect
+// from then on), so every later call reports the failure as well.
+int Engine::read_checks(cudaStream_t s) {
+  std::vector<int32_t> w((size_t)nsys());
+  if (w.empty()) return kOK;
+  CK(cudaMemcpyAsync(w.data(), d_checks_, sizeof(int32_t) * w.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < nsys(); ++k)
+    if (w[(size_t)k]) {
+      set_error("device check failed in system " + std::to_string(k) + " (check bits " + std::to_string(w[(size_t)k]) +
+                ")");
+      return kErrCheck;
+    }
   return kOK;
 }
 
@@ -1271,6 +1291,18 @@ int Engine::list_size(int k, int64_t* total, cudaStream_t s) {
   for (int32_t c : cnt) t += c;
   *total = t;
   return kOK;
+}
+
+int Engine::debug_set_list_word(int k, int64_t slot, int m, uint32_t word, cudaStream_t s) {
+  if (!kChecks) { set_error("list words can be written only in the checked build"); return kErrArg; }
+  if (!valid_id(k)) { set_error("no such system"); return kErrArg; }
+  const SysHost& h = sys_[k];
+  if (!h.has_state) { set_error("no state set"); return kErrState; }
+  CKR(ensure_lists(s));
+  if (slot < 0 || slot >= h.spec.n || m < 0 || m >= h.kmax) { set_error("slot or entry out of range"); return kErrArg; }
+  const int64_t w = list_word(h.l_off, (int)(slot / kTile), h.kmax, (int)(slot % kTile), m);
+  CK(cudaMemcpyAsync(d_.nbr + w, &word, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  return sync_check(s);
 }
 
 int Engine::get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s) {

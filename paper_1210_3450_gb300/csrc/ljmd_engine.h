@@ -53,7 +53,7 @@ struct ArenaCaps {
 
 // Status codes shared with the C ABI (same values as MD_*).
 enum : int { kOK = 0, kErrArg = -1, kErrOOM = -2, kErrOverflow = -3, kErrNonfinite = -4,
-             kErrTimeout = -5, kErrCuda = -6, kErrState = -7 };
+             kErrTimeout = -5, kErrCuda = -6, kErrState = -7, kErrCheck = -8 };
 
 void set_error(const std::string& msg);
 const char* last_error_cstr();
@@ -140,6 +140,8 @@ class Engine {
   // Inspection (host arrays, caller order).
   int get_cells(int k, int32_t* cell, cudaStream_t s);
   int list_size(int k, int64_t* total, cudaStream_t s);
+  // Checked build only: overwrite list entry m of sorted slot `slot` (a test of the checks).
+  int debug_set_list_word(int k, int64_t slot, int m, uint32_t word, cudaStream_t s);
   int get_list(int k, int64_t* start, int32_t* partners, cudaStream_t s);
 
   int set_active(int k, bool on);
@@ -183,6 +185,7 @@ class Engine {
   void drop_graphs();
   int run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s);
   int sync_check(cudaStream_t s);
+  int read_checks(cudaStream_t s);  // checked build: MD_ERR_CHECK if a device check failed
   DevArrays arrays() const;
   // Buffer holding system k's current positions.
   int cur_of(int k) const { return (!sys_[k].active && sys_[k].park >= 0) ? sys_[k].park : cur_; }
@@ -232,6 +235,7 @@ class Engine {
   SysStatus* d_status_ = nullptr;
   unsigned long long* d_disp2_ = nullptr;
   double* d_margin_ = nullptr;
+  int32_t* d_checks_ = nullptr;  // per system: failed device checks (checked build)
   int32_t* d_rebuild_ = nullptr;  // flags (nsys), compact ids (nsys), tile prefix (nsys + 1), chunk prefix (nsys + 1)
   int32_t* d_tile_sys_ = nullptr;
   double* d_obs_ = nullptr;

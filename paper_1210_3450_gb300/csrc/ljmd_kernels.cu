@@ -53,6 +53,17 @@ __device__ __forceinline__ bool tile_ctx(const DevArrays& a, TileCtx& t, SysPara
   return true;
 }
 
+// Slot of a listed partner (list word e); the checked build verifies it.
+__device__ __forceinline__ uint32_t partner_slot(const DevArrays& a, int sys, uint32_t e, int n, uint32_t self) {
+  const uint32_t j = e & kIdxMask;
+  return check_ok(a, sys, j < (uint32_t)n, kChkPartner) ? j : self;
+}
+// List length of a slot; the checked build verifies it against the capacity.
+__device__ __forceinline__ int list_count(const DevArrays& a, int sys, int64_t s, int kmax) {
+  const int cnt = a.ncnt[s];
+  return check_ok(a, sys, cnt >= 0 && cnt <= kmax, kChkCount) ? cnt : 0;
+}
+
 // Tile w of the rebuilding systems (in rebuild order; reb_pref holds the prefix of
 // their tile counts): false if its system is inactive.
 __device__ __forceinline__ bool reb_tile(const DevArrays& a, int nreb, int w, TileCtx& t, SysParams& P) {
@@ -153,6 +164,7 @@ __global__ void k_cell_count(DevArrays a, int cur) {
     int c = 0;
     if (P.nc > 1) {
       c = cell_of(w, P.inv_cs, P.nc);
+      if (!check_ok(a, t.sys, c >= 0 && c < P.nc * P.nc * P.nc, kChkCell)) c = 0;
       atomicAdd(&a.ccount[P.c_off + c], 1);
     }
     a.cell[t.s] = c;
@@ -281,6 +293,7 @@ __global__ void k_scatter(DevArrays a, int cur) {
     }
     const int c = a.cell[t.s];
     const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
+    if (!check_ok(a, t.sys, pos < a.cstart[P.c_off + c + 1], kChkScatter)) return;
     const int64_t d = P.p_off + pos;
     a.perm[d] = t.local;
     // x >= 0 (wrapped at the count), so its bit pattern orders like the value
@@ -317,6 +330,7 @@ __global__ void k_cell_rank(DevArrays a) {
       const long long kj = key[q];
       rank += (kj < ki || (kj == ki && idk[q] < idi)) ? 1 : 0;
     }
+    if (!check_ok(a, t.sys, lo + rank < hi, kChkRank)) return;
     a.perm2[P.p_off + lo + rank] = i;
   });
 }
@@ -328,7 +342,9 @@ __global__ void k_cell_rank(DevArrays a) {
 __global__ void k_gather(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
-    const int64_t old = P.p_off + a.perm2[t.s];
+    const int src = a.perm2[t.s];
+    if (!check_ok(a, t.sys, src >= 0 && src < P.n, kChkGather)) return;
+    const int64_t old = P.p_off + src;
     const double4_32a x = a.x[cur][old];
     a.xref[t.s] = x;
     int4 q = fixed4(x, P.qscale);
@@ -387,12 +403,24 @@ struct ListCtx {
   int count;
   int kmax;
   bool half;              // half list: only partners in higher slots
+  int32_t* chk;           // the system's check word (checked build)
+  // The checked build verifies each appended partner: a slot of the system, not
+  // the particle itself.
+  __device__ __forceinline__ bool entry_ok(uint32_t e) const {
+    if (!kChecks) return true;
+    const uint32_t j = e & kIdxMask;
+    if (j < (uint32_t)Pp->n && j != (uint32_t)li) return true;
+    atomicOr(chk, kChkListEntry);
+    return false;
+  }
   // Append e when p holds (a predicated store).
   __device__ __forceinline__ void push_if(bool p, uint32_t e) {
+    if (p && !entry_ok(e)) return;
     if (p && count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
     count += p ? 1 : 0;
   }
   __device__ __forceinline__ void push(uint32_t e) {
+    if (!entry_ok(e)) return;
     if (count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
     ++count;
   }
@@ -683,7 +711,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
     const bool act = li < n;
     const int64_t p_off = Pp->p_off;
     const int kmax = Pp->kmax;
-    ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0};
+    ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0,
+              a.checks + sys};
     if (act) copy_back_slot(a, cur, p_off + li);
     if (act) {
       if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
@@ -716,7 +745,7 @@ __device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int
   const unsigned actm = __ballot_sync(kFull, act);
   const int64_t p_off = Pp->p_off;
   const int kmax = Pp->kmax;
-  ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, false};
+  ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, false, a.checks + sys};
   if (act) copy_back_slot(a, cur, p_off + li);
   const int nc = Pp->nc;
   if (nc == 1) {
@@ -974,7 +1003,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
       Fx = f.x; Fy = f.y; Fz = f.z;
     }
   } else if (t.act) {
-    const int cnt = a.ncnt[t.s];
+    const int cnt = list_count(a, t.sys, t.s, P.kmax);
     const uint4* lp4 = (const uint4*)(a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0));
     const int4* qs = a.xq[cur] + P.p_off;
     const int4 qi = a.xq[cur][t.s];
@@ -1000,10 +1029,10 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
         ok[4 * u + 1] = rem > 1;
         ok[4 * u + 2] = rem > 2;
         ok[4 * u + 3] = rem > 3;
-        q[4 * u + 0] = ld_shadow(qs + (ok[4 * u + 0] ? (e[u].x & kIdxMask) : self), HINT);
-        q[4 * u + 1] = ld_shadow(qs + (ok[4 * u + 1] ? (e[u].y & kIdxMask) : self), HINT);
-        q[4 * u + 2] = ld_shadow(qs + (ok[4 * u + 2] ? (e[u].z & kIdxMask) : self), HINT);
-        q[4 * u + 3] = ld_shadow(qs + (ok[4 * u + 3] ? (e[u].w & kIdxMask) : self), HINT);
+        q[4 * u + 0] = ld_shadow(qs + (ok[4 * u + 0] ? partner_slot(a, t.sys, e[u].x, P.n, self) : self), HINT);
+        q[4 * u + 1] = ld_shadow(qs + (ok[4 * u + 1] ? partner_slot(a, t.sys, e[u].y, P.n, self) : self), HINT);
+        q[4 * u + 2] = ld_shadow(qs + (ok[4 * u + 2] ? partner_slot(a, t.sys, e[u].z, P.n, self) : self), HINT);
+        q[4 * u + 3] = ld_shadow(qs + (ok[4 * u + 3] ? partner_slot(a, t.sys, e[u].w, P.n, self) : self), HINT);
       }
 #pragma unroll
       for (int m = 0; m < 4 * GROUPS; ++m) pair_fp32(qi, q[m], ok[m], qu, rc2, c2x8, fx, fy, fz);
@@ -1075,14 +1104,14 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
       Fx = f.x; Fy = f.y; Fz = f.z;
     }
   } else if (t.act) {
-    const int cnt = a.ncnt[t.s];
+    const int cnt = list_count(a, t.sys, t.s, P.kmax);
     const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
     const double4_32a* xs = a.x[cur] + P.p_off;
     const long long rc2b = __double_as_longlong(P.rc2);
     const double c2x8 = 8.0 * P.c2, L = P.L;
     for (int k = 0; k < cnt; ++k) {
       const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
-      const double4_32a xj = xs[e & kIdxMask];
+      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
       double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
       const unsigned code = e >> kIdxBits;
       if (code) {
@@ -1124,7 +1153,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_half_fp64(DevArrays a, int cur,
   if (!tile_ctx(a, t, P) || !t.act) return;
   const int lane = threadIdx.x & 31;
   const double4_32a xi = a.x[cur][t.s];
-  const int cnt = a.ncnt[t.s];
+  const int cnt = list_count(a, t.sys, t.s, P.kmax);
   const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
   const double4_32a* xs = a.x[cur] + P.p_off;
   double4_32a* fa = a.facc + P.p_off;
@@ -1133,7 +1162,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_half_fp64(DevArrays a, int cur,
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
-    const uint32_t j = e & kIdxMask;
+    const uint32_t j = partner_slot(a, t.sys, e, P.n, (uint32_t)t.local);
     const double4_32a xj = xs[j];
     double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
     const unsigned code = e >> kIdxBits;
@@ -1170,7 +1199,7 @@ __global__ void __launch_bounds__(BLOCK) k_force_half_fp32(DevArrays a, int cur,
   SysParams P;
   if (!tile_ctx(a, t, P) || !t.act) return;
   const int lane = threadIdx.x & 31;
-  const int cnt = a.ncnt[t.s];
+  const int cnt = list_count(a, t.sys, t.s, P.kmax);
   const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
   const int4* qs = a.xq[cur] + P.p_off;
   const int4 qi = a.xq[cur][t.s];
@@ -1178,7 +1207,8 @@ __global__ void __launch_bounds__(BLOCK) k_force_half_fp32(DevArrays a, int cur,
   const float qu = P.qunit, rc2 = P.rc2f, c2x8 = 8.0f * P.c2f;
   float fx = 0.f, fy = 0.f, fz = 0.f;
   for (int k = 0; k < cnt; ++k) {
-    const uint32_t j = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3)) & kIdxMask;
+    const uint32_t j = partner_slot(a, t.sys, __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3)), P.n,
+                                    (uint32_t)t.local);
     float px = 0.f, py = 0.f, pz = 0.f;
     pair_fp32(qi, qs[j], true, qu, rc2, c2x8, px, py, pz);
     fx += px;
@@ -1242,7 +1272,7 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
   if (t.act && with_pairs) {
     const double4_32a xi = a.x[cur][t.s];
     const double4_32a* xs = a.x[cur] + P.p_off;
-    const int cnt = a.ncnt[t.s];
+    const int cnt = list_count(a, t.sys, t.s, P.kmax);
     const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
     const long long rc2b = __double_as_longlong(P.rc2);
     const long long tinyb = __double_as_longlong(1e-30);
@@ -1251,7 +1281,7 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
     int nin = 0;
     for (int k = 0; k < cnt; ++k) {
       const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
-      const double4_32a xj = xs[e & kIdxMask];
+      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
       double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
       const unsigned code = e >> kIdxBits;
       if (code) {
@@ -1308,12 +1338,12 @@ __global__ void __launch_bounds__(kBlock) k_pair_stats(DevArrays a, int cur, uns
   if (t.act) {
     const double4_32a xi = a.x[cur][t.s];
     const double4_32a* xs = a.x[cur] + P.p_off;
-    const int cnt = a.ncnt[t.s];
+    const int cnt = list_count(a, t.sys, t.s, P.kmax);
     const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
     listed = (unsigned)cnt;
     for (int k = 0; k < cnt; ++k) {
       const uint32_t e = lp[(int64_t)(k >> 2) * (4 * kTile) + (k & 3)];
-      const double4_32a xj = xs[e & kIdxMask];
+      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
       const unsigned code = e >> kIdxBits;
       const double dx = apply_image(xj.x - xi.x, code & 3u, P.L);
       const double dy = apply_image(xj.y - xi.y, (code >> 2) & 3u, P.L);

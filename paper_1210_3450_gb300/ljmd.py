@@ -22,6 +22,7 @@ MD_ERR_NONFINITE = -4
 MD_ERR_TIMEOUT = -5
 MD_ERR_CUDA = -6
 MD_ERR_STATE = -7
+MD_ERR_CHECK = -8
 MD_FP64 = 0
 MD_FP32_FORCE = 1
 MD_FP64_RCP8 = 2
@@ -45,10 +46,12 @@ TUNING_KEYS = {"step_block": MD_TUNE_STEP_BLOCK, "step_groups": MD_TUNE_STEP_GRO
 
 _ERRNAMES = {v: k for k, v in dict(MD_ERR_ARG=-1, MD_ERR_OOM=-2, MD_ERR_LIST_OVERFLOW=-3,
                                    MD_ERR_NONFINITE=-4, MD_ERR_TIMEOUT=-5, MD_ERR_CUDA=-6,
-                                   MD_ERR_STATE=-7).items()}
+                                   MD_ERR_STATE=-7, MD_ERR_CHECK=-8).items()}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libljmd.so")
+# the same library with device bounds checks (a test and debugging tool)
+CHECKED_LIB_PATH = os.path.join(_HERE, "_build", "checked", "libljmd.so")
 
 _lib = None
 _P = C.c_void_p
@@ -83,6 +86,7 @@ SIGNATURES = {
     "md_build_list": (C.c_int, [_P]),
     "md_get_cells": (C.c_int, [_P, _PI32, _PI32]),
     "md_list_size": (C.c_int, [_P, _PI64]),
+    "md_debug_set_list_word": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_uint32]),
     "md_get_list": (C.c_int, [_P, _PI64, _PI32]),
     "md_pair_stats": (C.c_int, [_P, _PI64, _PI64]),
     "md_bubbles": (C.c_int, [_P, C.c_double, C.c_double, _PI32, C.POINTER(C.c_uint8), _PI64, _PI64, C.c_int64]),
@@ -313,6 +317,10 @@ class LJSystem:
         nc = C.c_int32()
         _check(_lib.md_get_cells(self._h, cell.ctypes.data_as(_PI32), C.byref(nc)))
         return cell, nc.value
+
+    def debug_set_list_word(self, slot: int, entry: int, word: int):
+        """Checked build only: overwrite one raw list word (a test of the device checks)."""
+        _check(_lib.md_debug_set_list_word(self._h, int(slot), int(entry), int(word) & 0xFFFFFFFF))
 
     def list_size(self) -> int:
         t = C.c_int64()
