@@ -678,6 +678,12 @@ int Engine::get_state_dev(int k, double* x, double* v, cudaStream_t s) {
   return kOK;
 }
 
+bool Engine::any_active() const {
+  for (const SysHost& h : sys_)
+    if (h.used && h.active) return true;
+  return false;
+}
+
 int Engine::sync_check(cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   collect_timing();
@@ -1045,7 +1051,7 @@ int Engine::step(int64_t nsteps, const std::vector<double>& dt, cudaStream_t s) 
     if (!std::isfinite(dt[k])) { set_error("dt must be finite"); return kErrArg; }
     sys_[k].dt = dt[k];
   }
-  if (nsteps == 0) return kOK;
+  if (nsteps == 0 || !any_active()) return kOK;  // an empty or fully paused arena: nothing to do
   CKR(upload_params());
   CKR(ensure_lists(s));
   CKR(ensure_forces(s));
@@ -1166,6 +1172,7 @@ int Engine::step_nvt(int64_t nsteps, const std::vector<double>& dt, const std::v
       return kErrArg;
     }
   }
+  if (nsteps == 0 || !any_active()) return kOK;
   std::vector<double> o3((size_t)(3 * ns)), fac((size_t)ns, 1.0);
   // `halves` consecutive thermostat half steps from one kinetic-energy reduction:
   // each is zeta += dt/4 G, eta += dt/2 zeta, v *= exp(-dt/2 zeta), zeta += dt/4 G'

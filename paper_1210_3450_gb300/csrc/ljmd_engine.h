@@ -185,6 +185,7 @@ class Engine {
   void drop_graphs();
   int run_graph(int64_t nsteps, int first_flags, int64_t* done, cudaStream_t s);
   int sync_check(cudaStream_t s);
+  bool any_active() const;  // some system takes part in launches
   int read_checks(cudaStream_t s);  // checked build: MD_ERR_CHECK if a device check failed
   DevArrays arrays() const;
   // Buffer holding system k's current positions.

@@ -1441,8 +1441,9 @@ __global__ void __launch_bounds__(256) k_obs_final(const int32_t* __restrict__ w
 // ---------------------------------------------------------------- launchers
 
 namespace {
+// At least one block: with no tiles its warps return at once (an empty arena).
 inline unsigned tile_blocks(const DevArrays& a) {
-  return (unsigned)(((int64_t)a.ntiles * kTile + kBlock - 1) / kBlock);
+  return (unsigned)std::max<int64_t>(1, ((int64_t)a.ntiles * kTile + kBlock - 1) / kBlock);
 }
 }  // namespace
 
@@ -1629,7 +1630,7 @@ void launch_decide(const DevArrays& a, int nsys, int fp32, int vflag, int32_t* r
                    int32_t* reb_pref, int32_t* reb_count, cudaGraphConditionalHandle h_if,
                    cudaGraphConditionalHandle h_loop, int last, cudaStream_t s) {
   // one block; as many warps as the systems need (a single warp for one system)
-  const int threads = std::min(1024, (nsys + 31) / 32 * 32);
+  const int threads = std::max(32, std::min(1024, (nsys + 31) / 32 * 32));
   k_decide<<<1, threads, 0, s>>>(a, nsys, fp32, vflag, rebuild, rebuild_ids, reb_pref, reb_count, h_if, h_loop,
                                  last);
 }
@@ -1656,7 +1657,7 @@ void launch_cell_rank(const DevArrays& a, cudaStream_t s) { k_cell_rank<<<bin_bl
 void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<bin_blocks(a), kBlock, 0, s>>>(a, cur); }
 namespace {
 inline unsigned blocks_of(const DevArrays& a, int block) {
-  return (unsigned)(((int64_t)a.ntiles * kTile + block - 1) / block);
+  return (unsigned)std::max<int64_t>(1, ((int64_t)a.ntiles * kTile + block - 1) / block);
 }
 }  // namespace
 

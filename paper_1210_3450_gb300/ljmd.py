@@ -504,6 +504,18 @@ class LJBatch:
         arr = self._dt(dt)
         _check(_lib.md_batch_step_async(self._h, int(nsteps), _pd(arr), _stream_ptr(stream)))
 
+    def step_nvt(self, nsteps: int, dt, temperature, q, zeta=None, eta=None):
+        """Nose-Hoover NVT steps of every active system (md_batch_step_nvt): dt,
+        temperature and q per system (scalars, sequences or {id: value}); zeta and eta
+        (max_systems arrays, zero if None) are updated and returned."""
+        dts, ts, qs = self._dt(dt), self._dt(temperature), self._dt(q)
+        z = np.zeros(self.max_systems) if zeta is None else np.ascontiguousarray(zeta, dtype=np.float64).copy()
+        e = np.zeros(self.max_systems) if eta is None else np.ascontiguousarray(eta, dtype=np.float64).copy()
+        if z.shape != (self.max_systems,) or e.shape != (self.max_systems,):
+            raise ValueError(f"zeta and eta need {self.max_systems} entries")
+        _check(_lib.md_batch_step_nvt(self._h, int(nsteps), _pd(dts), _pd(ts), _pd(qs), _pd(z), _pd(e)))
+        return z, e
+
     def forces(self, sid: int) -> np.ndarray:
         f = np.empty((self._n[sid], 3))
         _check(_lib.md_batch_forces(self._h, int(sid), _pd(f)))

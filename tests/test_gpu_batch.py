@@ -166,3 +166,36 @@ def test_paused_system_resumes_exactly(ljmd, graph):
         xa, va = s.get_state()
     np.testing.assert_array_equal(xa, xb)
     np.testing.assert_array_equal(va, vb)
+
+
+def test_empty_and_paused_arena_steps_are_no_ops(ljmd):
+    """Stepping an arena with no systems, or with every system paused, does nothing
+    and succeeds; a system added afterwards steps as it does alone."""
+    x, box = li.perturbed_fcc(700, 0.8, 0.1, 631)
+    v = li.maxwell_boltzmann(700, 0.9, 632)
+    b = ljmd.LJBatch(arena=dict(slots=4096, cells=4096, list_words=1 << 20, max_systems=4),
+                     precision=ljmd.MD_FP32_FORCE)
+    try:
+        b.step(5, [0.005] * b.max_systems)
+        b.step_nvt(4, [0.005] * b.max_systems, [1.0] * b.max_systems, [1.0] * b.max_systems)
+        sid = b.add(700, box, 2.5, 0.3)
+        b.set_state(sid, x, v)
+        before = b.get_state(sid)
+        b.set_active(sid, False)
+        b.step(5, [0.005] * b.max_systems)
+        b.set_active(sid, True)
+        after = b.get_state(sid)
+        np.testing.assert_array_equal(after[0], before[0])
+        np.testing.assert_array_equal(after[1], before[1])
+        b.step(20, [0.005] * b.max_systems)
+        got = b.get_state(sid)
+        b.remove(sid)
+        b.step(3, [0.005] * b.max_systems)
+    finally:
+        b.close()
+    with ljmd.LJSystem(box, 700, 2.5, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state(x, v)
+        s.step(20, 0.005)
+        ref = s.get_state()
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
