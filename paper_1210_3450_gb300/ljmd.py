@@ -485,6 +485,12 @@ class LJBatch:
         _check(_lib.md_batch_get_state(self._h, int(sid), _pd(x), _pd(v)))
         return x, v
 
+    def get_state_dev(self, sid: int, x=None, v=None, stream=None):
+        """Positions and velocities of system sid into CUDA tensors (caller order)."""
+        n = self._n[sid]
+        _check(_lib.md_batch_get_state_dev(self._h, int(sid), _dev_ptr(x, n) if x is not None else None,
+                                           _dev_ptr(v, n) if v is not None else None, _stream_ptr(stream)))
+
     def _dt(self, dt):
         arr = np.zeros(self.max_systems)
         if np.isscalar(dt):

@@ -199,3 +199,39 @@ def test_empty_and_paused_arena_steps_are_no_ops(ljmd):
         ref = s.get_state()
     np.testing.assert_array_equal(got[0], ref[0])
     np.testing.assert_array_equal(got[1], ref[1])
+
+
+def test_device_state_calls_match_host_calls(ljmd):
+    """set_state_dev / get_state_dev (CUDA tensors, caller order) give the same
+    state as the host-array calls, for one system and for a system of a batch."""
+    import torch
+    x, box = li.perturbed_fcc(1500, 0.8, 0.1, 641)
+    v = li.maxwell_boltzmann(1500, 0.9, 642)
+    xd = torch.tensor(x, device="cuda")
+    vd = torch.tensor(v, device="cuda")
+    with ljmd.LJSystem(box, 1500, 2.5, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state_dev(xd, vd)
+        s.step(30, 0.005)
+        xo, vo = torch.empty_like(xd), torch.empty_like(vd)
+        s.get_state_dev(xo, vo)
+        torch.cuda.synchronize()
+        xh, vh = s.get_state()
+    np.testing.assert_array_equal(xo.cpu().numpy(), xh)
+    np.testing.assert_array_equal(vo.cpu().numpy(), vh)
+    b = ljmd.LJBatch(systems=[(700, li.box_length(700, 0.8), 2.5, 0.3), (1500, box, 2.5, 0.3)],
+                     precision=ljmd.MD_FP32_FORCE)
+    try:
+        x0, b0 = li.perturbed_fcc(700, 0.8, 0.1, 643)
+        b.set_state(0, x0, li.maxwell_boltzmann(700, 0.9, 644))
+        b.set_state_dev(1, xd, vd)
+        b.step(30, [0.005, 0.005])
+        xo2, vo2 = torch.empty_like(xd), torch.empty_like(vd)
+        b.get_state_dev(1, xo2, vo2)
+        torch.cuda.synchronize()
+        xb, vb = b.get_state(1)
+    finally:
+        b.close()
+    np.testing.assert_array_equal(xo2.cpu().numpy(), xb)
+    np.testing.assert_array_equal(vo2.cpu().numpy(), vb)
+    np.testing.assert_array_equal(xb, xh)   # the same system, alone and in a batch
+    np.testing.assert_array_equal(vb, vh)
