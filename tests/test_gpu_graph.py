@@ -105,6 +105,32 @@ def test_overflow_inside_graph_grows_and_resumes(ljmd, oracle):
     np.testing.assert_array_equal(st1, ostart)
 
 
+def test_overflow_in_a_batch_equals_host_loop(ljmd):
+    """The same contracting gas in a batch beside a fluid: the graph's rebuild pass
+    overflows for the gas only; after the host grows its list, both systems end bit
+    for bit where the host-driven loop puts them."""
+    n = 1372
+    xg, boxg = li.perturbed_fcc(n, 0.0556, 0.1, 706)
+    vg = -0.38 * (xg - 0.5 * boxg)
+    xf, boxf = li.perturbed_fcc(4000, 0.8442, 0.08, 708)
+    vf = li.maxwell_boltzmann(4000, 1.1, 709)
+    out = []
+    for graph in (0, 1):
+        b = ljmd.LJBatch(systems=[(n, boxg, 2.5, 0.3), (4000, boxf, 2.5, 0.3)], precision=ljmd.MD_FP32_FORCE)
+        try:
+            b.set_tuning(graph=graph)
+            b.set_state(0, xg, vg)
+            b.set_state(1, xf, vf)
+            b.step(300, [0.005, 0.005])
+            out.append([b.get_state(k) + (b.stats(k),) for k in range(2)])
+        finally:
+            b.close()
+    for (x0, v0, s0), (x1, v1, s1) in zip(*out):
+        np.testing.assert_array_equal(x0, x1)
+        np.testing.assert_array_equal(v0, v1)
+        assert s0 == s1
+
+
 def test_nonfinite_stops_graph_loop(ljmd):
     x = li.uniform_positions(500, 20.0, 707)
     v = np.zeros_like(x)
