@@ -353,6 +353,13 @@ MD_API int md_batch_set_state_dev(md_batch* b, int id, const double* x_dev, cons
 MD_API int md_batch_get_state(md_batch* b, int id, double* x, double* v);
 MD_API int md_batch_get_state_dev(md_batch* b, int id, double* x_dev, double* v_dev, void* stream);
 
+/* Exact checkpoint of system id, as md_get_checkpoint / md_set_checkpoint: a system can
+ * be saved, evicted and resumed later (in this batch, another one, or an md_ctx with the
+ * same N, L, rc, skin and settings), continuing bit for bit as if never interrupted. */
+MD_API int md_batch_get_checkpoint(md_batch* b, int id, double* x, double* v, double* x_build, double* margin);
+MD_API int md_batch_set_checkpoint(md_batch* b, int id, const double* x, const double* v, const double* x_build,
+                                   double margin);
+
 /* Advance every active system by nsteps velocity-Verlet steps; dt[id] is the time
  * step of system id (an array of max_systems doubles; entries of inactive ids are
  * ignored). Blocks until done. */

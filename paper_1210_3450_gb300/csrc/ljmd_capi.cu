@@ -594,6 +594,46 @@ int md_batch_get_state(md_batch* b, int id, double* x, double* v) {
   return MD_OK;
 }
 
+int md_batch_get_checkpoint(md_batch* b, int id, double* x, double* v, double* xref, double* margin) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  if (!x || !v || !xref || !margin) {
+    set_error("null checkpoint array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = b->eng.sys(id).spec.n;
+  double* st = nullptr;
+  if ((r = b->eng.stage(n, &st))) return r;
+  double m = 0.0;
+  if ((r = b->eng.get_checkpoint_dev(id, nullptr, nullptr, st, &m, b->stream))) return r;
+  if ((r = bd2h(b, xref, st, 3 * n))) return r;
+  if ((r = b->eng.get_checkpoint_dev(id, st, st + 3 * n, nullptr, nullptr, b->stream))) return r;
+  if ((r = bd2h(b, x, st, 3 * n))) return r;
+  if ((r = bd2h(b, v, st + 3 * n, 3 * n))) return r;
+  *margin = m;
+  return MD_OK;
+}
+
+int md_batch_set_checkpoint(md_batch* b, int id, const double* x, const double* v, const double* xref,
+                            double margin) {
+  int r = check_batch(b);
+  if (r) return r;
+  if ((r = check_id(b, id))) return r;
+  if (!x || !v || !xref) {
+    set_error("null checkpoint array");
+    return MD_ERR_ARG;
+  }
+  const int64_t n = b->eng.sys(id).spec.n;
+  double* st = nullptr;
+  if ((r = b->eng.stage(n, &st))) return r;
+  if ((r = bh2d(b, st, xref, 3 * n))) return r;
+  if ((r = bh2d(b, st + 3 * n, v, 3 * n))) return r;
+  if ((r = b->eng.set_checkpoint_dev(id, st, st + 3 * n, b->stream))) return r;
+  if ((r = bh2d(b, st, x, 3 * n))) return r;
+  return b->eng.finish_checkpoint_dev(id, st, margin, b->stream);
+}
+
 int md_batch_get_state_dev(md_batch* b, int id, double* x, double* v, void* stream) {
   int r = check_batch(b);
   if (r) return r;

@@ -86,6 +86,8 @@ SIGNATURES = {
     "md_build_list": (C.c_int, [_P]),
     "md_get_cells": (C.c_int, [_P, _PI32, _PI32]),
     "md_list_size": (C.c_int, [_P, _PI64]),
+    "md_batch_get_checkpoint": (C.c_int, [_P, C.c_int, _PD, _PD, _PD, _PD]),
+    "md_batch_set_checkpoint": (C.c_int, [_P, C.c_int, _PD, _PD, _PD, C.c_double]),
     "md_debug_set_list_word": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_uint32]),
     "md_get_list": (C.c_int, [_P, _PI64, _PI32]),
     "md_pair_stats": (C.c_int, [_P, _PI64, _PI64]),
@@ -484,6 +486,20 @@ class LJBatch:
         x, v = _out3(out, self._n[sid])
         _check(_lib.md_batch_get_state(self._h, int(sid), _pd(x), _pd(v)))
         return x, v
+
+    def checkpoint(self, sid: int) -> dict:
+        """Exact checkpoint of system sid (see LJSystem.checkpoint)."""
+        n = self._n[sid]
+        x, v, xb = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+        m = C.c_double()
+        _check(_lib.md_batch_get_checkpoint(self._h, int(sid), _pd(x), _pd(v), _pd(xb), C.byref(m)))
+        return dict(x=x, v=v, x_build=xb, margin=m.value)
+
+    def restore(self, sid: int, ck: dict):
+        """Restore a checkpoint into system sid (same sizes and settings)."""
+        n = self._n[sid]
+        x, v, xb = _host3(ck["x"], n), _host3(ck["v"], n), _host3(ck["x_build"], n)
+        _check(_lib.md_batch_set_checkpoint(self._h, int(sid), _pd(x), _pd(v), _pd(xb), float(ck["margin"])))
 
     def get_state_dev(self, sid: int, x=None, v=None, stream=None):
         """Positions and velocities of system sid into CUDA tensors (caller order)."""

@@ -55,3 +55,48 @@ def test_checkpoint_right_after_set_state(ljmd):
         with pytest.raises(ljmd.MDError) as e:
             s.checkpoint()
         assert e.value.code == ljmd.MD_ERR_STATE
+
+
+def test_batch_checkpoint_moves_a_system(ljmd):
+    """A system of a batch checkpointed mid-run and resumed in another batch (beside
+    systems at other points of their runs) and in a single context continues bit for
+    bit as the uninterrupted run: the eviction and resumption a server does."""
+    specs, states = [], []
+    for n, rho, seed in [(1200, 0.8, 1111), (3000, 0.75, 1113), (800, 0.85, 1115)]:
+        x, box = li.perturbed_fcc(n, rho, 0.08, seed)
+        specs.append((n, box, 2.5, 0.3))
+        states.append((x, li.maxwell_boltzmann(n, 1.0, seed + 1)))
+    dts = [0.005, 0.004, 0.005]
+
+    def batch():
+        b = ljmd.LJBatch(systems=specs, precision=ljmd.MD_FP32_FORCE)
+        for k, (x, v) in enumerate(states):
+            b.set_state(k, x, v)
+        return b
+
+    a = batch()
+    try:
+        a.step(97, dts)
+        ck = a.checkpoint(1)
+        a.step(60, dts)
+        ref = a.get_state(1)
+    finally:
+        a.close()
+    c = batch()
+    try:
+        c.step(13, dts)                     # the others are elsewhere in their runs
+        c.restore(1, ck)
+        c.step(60, dts)
+        got = c.get_state(1)
+    finally:
+        c.close()
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[1], ref[1])
+    n, box = specs[1][0], specs[1][1]
+    with ljmd.LJSystem(box, n, 2.5, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state(*states[1])
+        s.restore(ck)
+        s.step(60, 0.004)
+        alone = s.get_state()
+    np.testing.assert_array_equal(alone[0], ref[0])
+    np.testing.assert_array_equal(alone[1], ref[1])
