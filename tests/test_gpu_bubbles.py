@@ -41,3 +41,26 @@ def test_bubbles_match_oracle(ljmd, oracle, name, x, box):
     np.testing.assert_array_equal(g["sizes"], ref["sizes"])
     if name == "three-cavities":
         assert g["n_bubbles"] == 3
+
+
+def test_bubbles_in_an_expanded_liquid(ljmd, oracle):
+    """The cavitation protocol at 864,000 particles: an FCC 60^3 x 4 lattice at rho
+    0.70 with T = 0.9 velocities, expanded by 1.05 per axis (rho 0.605) and run 2000
+    FP32-force steps with rc 3.0. Gas subcells then form many clusters of every size;
+    counts, cluster count and sizes equal the oracle's at the final positions."""
+    n = 864000
+    x, box = li.perturbed_fcc(n, 0.70, 0.1, 721)
+    v = li.maxwell_boltzmann(n, 0.9, 722)
+    x = x * 1.05
+    box = box * 1.05
+    with ljmd.LJSystem(box, n, 3.0, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state(x, v)
+        s.step(2000, 0.005)
+        g = s.bubbles(3.0, 0.2)
+        xw, _ = s.get_state()
+    ref = oracle.bubbles(xw, box, 3.0, 0.2)
+    assert ref["n_bubbles"] >= 20
+    assert g["ns"] == ref["ns"]
+    np.testing.assert_array_equal(g["counts"], np.minimum(ref["counts"], 255).astype(np.uint8))
+    assert g["n_bubbles"] == ref["n_bubbles"]
+    np.testing.assert_array_equal(g["sizes"], ref["sizes"])
