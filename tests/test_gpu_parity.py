@@ -160,6 +160,20 @@ def test_observables_match_oracle(ljmd, oracle, precision):
         assert o[k] == pytest.approx(r[k], rel=1e-12), k
 
 
+def test_full_size_observables(ljmd, oracle):
+    """PE, W, KE, T and P of the 2,048,000-particle fluid (FCC 80^3 x 4 displaced by up
+    to 0.1, T 0.722) against the oracle's list-based sums, both force forms (the
+    observables are FP64 in both): relative 1e-12."""
+    x, box = li.perturbed_fcc(2_048_000, 0.8442, 0.1, 112)
+    v = li.maxwell_boltzmann(2_048_000, 0.722, 123)
+    r = oracle.observables(x, v, box, 2.5)
+    for precision in (0, 1):
+        with make(ljmd, x, v, box, precision=precision) as s:
+            o = s.observables()
+        for k in ["pe", "virial", "ke", "temperature", "pressure"]:
+            assert o[k] == pytest.approx(r[k], rel=1e-12), (precision, k)
+
+
 def test_trajectory_200_steps_fp64(ljmd, oracle):
     """The N = 4000 fluid (FCC, rho 0.8442, T 0.722, dt 0.005) for 200 steps."""
     cfg = li.config_small_fluid()
