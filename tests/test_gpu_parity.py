@@ -193,6 +193,25 @@ def test_trajectory_200_steps_fp64(ljmd, oracle):
     assert og["pe"] == pytest.approx(ro["pe"], rel=1e-10)
 
 
+def test_full_size_trajectory_fp64(ljmd, oracle):
+    """The 2,048,000-particle fluid (FCC 80^3 x 4, the benchmark's configuration) for 12
+    FP64 steps, one list rebuild inside: every position and velocity against the oracle
+    (the same bars as the 200-step run), and the same rebuild count."""
+    cfg = li.config_large_fluid()
+    steps = 12
+    with make(ljmd, cfg.x, cfg.v, cfg.box) as s:
+        s.step(steps, cfg.dt)
+        xg, vg = s.get_state()
+        st = s.stats()
+    r = oracle.run(cfg.x, cfg.v, cfg.box, cfg.rc, cfg.skin, steps, cfg.dt)
+    assert r["rebuilds"] >= 2
+    d = xg - r["x"]
+    d -= cfg.box * np.round(d / cfg.box)
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(vg - r["v"]).max() < 1e-9
+    assert st["rebuilds"] == r["rebuilds"]
+
+
 def test_state_into_caller_arrays(ljmd):
     """get_state(out=(x, v)) fills pinned host arrays with the same values as
     get_state()."""
