@@ -274,7 +274,13 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
  *                        control words once per launch; 0: the host decides after
  *                        every step. Results are identical. Timing (md_set_timing)
  *                        uses the host-driven loop.
- * Defaults 128 / 2 / 128 / 0 / 1 / 1. The autotuner (paper_1210_3450_gb300.autotune) times the
+ *   MD_TUNE_FP64_QUEUE   1: the FP64 force loops classify each listed pair on the
+ *                        fixed-point shadow positions first and run the FP64
+ *                        arithmetic only for the pairs that may be inside rc, taken
+ *                        from a per-thread queue in list order, so that warps run
+ *                        it with full lanes; 0: one plain loop over the list.
+ *                        Results are identical bit for bit.
+ * Defaults 128 / 2 / 128 / 0 / 1 / 1 / 1. The autotuner (paper_1210_3450_gb300.autotune) times the
  * choices on the caller's own systems and sets the fastest. */
 #define MD_TUNE_STEP_BLOCK 0
 #define MD_TUNE_STEP_GROUPS 1
@@ -282,6 +288,7 @@ MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, doubl
 #define MD_TUNE_LIST_VARIANT 3
 #define MD_TUNE_STEP_HINT 4
 #define MD_TUNE_GRAPH 5
+#define MD_TUNE_FP64_QUEUE 6
 MD_API int md_set_tuning(md_ctx* ctx, int key, int value);
 MD_API int md_get_tuning(md_ctx* ctx, int key, int* value);
 

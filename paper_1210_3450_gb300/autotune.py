@@ -25,6 +25,7 @@ STEP_GROUPS = (1, 2)
 STEP_HINTS = (0, 1)
 LIST_BLOCKS = (64, 128, 256)
 LIST_VARIANTS = (0, 1, 2, 3, 4)
+FP64_QUEUE = (0, 1)
 
 
 def shape_key(precision: int, particles: int, density: float, systems: int) -> str:
@@ -57,19 +58,25 @@ def tune(system, dt, key: str | None = None, steps: int = 30, cache: str | None 
         if known:
             system.set_tuning(**known["tuning"])
             return known
+    # FP32-force form: partner groups and cache hints; FP64 forms: the queued or
+    # plain force loop
     step_choices = list(itertools.product(STEP_BLOCKS, STEP_GROUPS if fp32 else (1,),
-                                          STEP_HINTS if fp32 else (0,)))
+                                          STEP_HINTS if fp32 else (0,), (1,) if fp32 else FP64_QUEUE))
     results = {}
     system.step(5, dt)
-    for blk, grp, hint in step_choices:
-        system.set_tuning(step_block=blk, step_groups=grp, step_hint=hint)
+
+    def name(c):
+        return f"step{c[0]}x{c[1]}h{c[2]}q{c[3]}"
+
+    for c in step_choices:
+        system.set_tuning(step_block=c[0], step_groups=c[1], step_hint=c[2], fp64_queue=c[3])
         system.step(2, dt)
         system.set_timing(True)
         system.step(steps, dt)
         t = system.get_timing()
-        results[f"step{blk}x{grp}h{hint}"] = t["step_ms"] / max(t["step_launches"], 1)
-    blk, grp, hint = min(step_choices, key=lambda c: results[f"step{c[0]}x{c[1]}h{c[2]}"])
-    system.set_tuning(step_block=blk, step_groups=grp, step_hint=hint)
+        results[name(c)] = t["step_ms"] / max(t["step_launches"], 1)
+    best = min(step_choices, key=lambda c: results[name(c)])
+    system.set_tuning(step_block=best[0], step_groups=best[1], step_hint=best[2], fp64_queue=best[3])
     list_times = {}
     for lb, lv in itertools.product(LIST_BLOCKS, LIST_VARIANTS):
         system.set_tuning(list_block=lb, list_variant=lv)

@@ -48,6 +48,7 @@ struct SysParams {
   float rl2q_hi;     // rl^2 (1 + 1e-5) in fixed-point units^2: certainly outside above
   float rl2f_lo;     // rl^2 (1 - eps(L / rl)) as float: the float pre-test's sure inside
   float rl2f_hi;     // rl^2 (1 + eps(L / rl)) as float: the float pre-test's sure outside
+  float rc2q_hi;     // rc^2 (1 + 1e-5) in fixed-point units^2: surely outside rc above (FP64 force loop)
   float rc2f;        // rc^2 as float (FP32 force cutoff)
   float c2f;         // c2 as float
   double skin;       // list margin (validity rule 2 d_max >= skin)
@@ -173,6 +174,7 @@ struct Tuning {
   int list_block = 128;
   int list_variant = 0;  // 0..3 per thread (bit 0: fixed-point pre-test; bit 1: row pruning); 4 per warp
   int step_hint = 1;     // 1: L1 eviction hints on the FP32 step kernel's loads
+  int fp64_queue = 1;    // 1: FP64 force loop classifies pairs first and queues the maybe-inside ones
 };
 
 // ---------------------------------------------------------------- launchers

@@ -125,6 +125,11 @@ int Engine::set_tuning(int key, int value) {
       if (value != 0 && value != 1) break;
       graph_ = value != 0;
       return kOK;
+    case 6:
+      if (value != 0 && value != 1) break;
+      tuning_.fp64_queue = value;
+      ++struct_ver_;
+      return kOK;
     default:
       break;
   }
@@ -134,7 +139,8 @@ int Engine::set_tuning(int key, int value) {
 
 int Engine::get_tuning(int key) const {
   return key == 0 ? tuning_.step_block : key == 1 ? tuning_.step_groups : key == 2 ? tuning_.list_block
-         : key == 3 ? tuning_.list_variant : key == 4 ? tuning_.step_hint : key == 5 ? (graph_ ? 1 : 0) : -1;
+         : key == 3 ? tuning_.list_variant : key == 4 ? tuning_.step_hint : key == 5 ? (graph_ ? 1 : 0)
+         : key == 6 ? tuning_.fp64_queue : -1;
 }
 
 int Engine::set_timing(bool on) {
@@ -533,6 +539,7 @@ int Engine::upload_params(int only) {
     P.qunit = (float)(h.spec.L / 4294967296.0);
     P.rl2q_lo = (float)(P.rl2 * P.qscale * P.qscale * (1.0 - 1e-5));
     P.rl2q_hi = (float)(P.rl2 * P.qscale * P.qscale * (1.0 + 1e-5));
+    P.rc2q_hi = (float)(P.rc2 * P.qscale * P.qscale * (1.0 + 1e-5));
     {
       // Float pre-test of the list build: candidate and key positions rounded to
       // float (error <= 2^-24 L, key shifted by an image <= 2^-23 L), so each

@@ -919,6 +919,8 @@ __device__ __forceinline__ unsigned long long integrate(const DevArrays& a, cons
     if (flags & kStepVmax) return v2b;
     return (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey) + (unsigned long long)(ez * ez);
   }
+  // the fixed-point shadow, which the FP64 force loop's pre-classification reads
+  a.xq[cur ^ 1][t.s] = fixed4(xn, P.qscale);
   if (flags & kStepVmax) return v2b;
   // exact FP64 check, the same operations as the reference
   const double4_32a r = a.xref[t.s];
@@ -1046,10 +1048,6 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
   warp_max_disp(a, t.sys, d2b, flags);
 }
 
-// FP64 form. The FP64 pipe is the bound: per listed pair 3 DADD + 3 (r^2); per
-// pair inside rc the reciprocal (3 DFMA after an integer-built FP32 seed),
-// powers (3), factor (2) and accumulation (3). The cutoff test compares bit
-// patterns (r^2 >= 0), so it costs no FP64 instruction.
 // Approximate reciprocal of r^2 for the force variants of Sec. 3.3: r^2 rounded
 // to float, its correctly rounded float reciprocal, the mantissa cut to 8 bits
 // for the stand-in of SPARC64 frcpad (relative error < 1/256, Eq. 2).
@@ -1085,15 +1083,36 @@ __device__ __forceinline__ double force_factor(double r2, double c2x8) {
   return fma(24.0, ir8, fma(-48.0, ir14, c2x8));
 }
 
-template <int BLOCK, int MODE>
+// FP64 form. The FP64 pipe is the bound (on GB300 a warp's FP64 instruction
+// holds the pipe about as long as 60 other instructions take to issue), and a
+// warp pays for an FP64 instruction whether one lane or all 32 need it. So each
+// thread first classifies its listed partners on their fixed-point shadow
+// positions (integer separations, float r^2, no FP64 instruction) against
+// rc^2 (1 + 1e-5), a bound that no pair inside rc can exceed (each shadow
+// coordinate errs by at most half a unit of L / 2^32, and the float r^2 by a few
+// parts in 1e7), and queues the list words of the pairs that
+// may be inside in shared memory. The FP64 work then runs in rounds in which every
+// thread with partners left takes the next pair of its own queue: per pair 3 DADD
+// for the separation and 3 for r^2, the exact test r^2 < rc^2 (bit patterns,
+// r^2 >= 0), and for pairs inside the reciprocal (3 DFMA after an integer-built
+// FP32 seed), the powers and factor (5) and the accumulation (3). A thread's
+// queue keeps list order and the pairs left out are outside rc, where the force
+// is zero, so every force is summed in the same order as a plain loop over the
+// list: the results are the same bit for bit.
+constexpr int kQueue64 = 16;  // queued list words per thread (FP64 force loop)
+
+// QUEUE false: the plain loop over the list (every listed pair takes the FP64
+// separation and r^2, the warp pays the force body whenever one lane is inside).
+template <int BLOCK, int MODE, bool QUEUE>
 __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, double ka, double kb, int flags) {
+  __shared__ uint32_t qbuf[QUEUE ? kQueue64 : 1][BLOCK];  // entry q of thread t at [q][t]: no bank conflicts
   if (a.ctl) {  // graph-captured loop (uniform over the grid)
     if (a.ctl->abort) return;
     flags = a.ctl->flags;
   }
   TileCtx t;
   SysParams P;
-  if (!tile_ctx(a, t, P)) return;
+  if (!tile_ctx(a, t, P)) return;  // uniform over the warp
   const int lane = threadIdx.x & 31;
   double Fx = 0.0, Fy = 0.0, Fz = 0.0;
   double4_32a xi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
@@ -1103,28 +1122,90 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
       const double4_32a f = a.f[t.s];
       Fx = f.x; Fy = f.y; Fz = f.z;
     }
-  } else if (t.act) {
-    const int cnt = list_count(a, t.sys, t.s, P.kmax);
-    const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
-    const double4_32a* xs = a.x[cur] + P.p_off;
-    const long long rc2b = __double_as_longlong(P.rc2);
-    const double c2x8 = 8.0 * P.c2, L = P.L;
-    for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
-      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
-      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-      const unsigned code = e >> kIdxBits;
-      if (code) {
-        dx = apply_image(dx, code & 3u, L);
-        dy = apply_image(dy, (code >> 2) & 3u, L);
-        dz = apply_image(dz, (code >> 4) & 3u, L);
+  } else if (!QUEUE) {
+    if (t.act) {
+      const int cnt = list_count(a, t.sys, t.s, P.kmax);
+      const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+      const double4_32a* xs = a.x[cur] + P.p_off;
+      const long long rc2b = __double_as_longlong(P.rc2);
+      const double c2x8 = 8.0 * P.c2, L = P.L;
+      for (int k = 0; k < cnt; ++k) {
+        const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
+        const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
+        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        const unsigned code = e >> kIdxBits;
+        if (code) {
+          dx = apply_image(dx, code & 3u, L);
+          dy = apply_image(dy, (code >> 2) & 3u, L);
+          dz = apply_image(dz, (code >> 4) & 3u, L);
+        }
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (__double_as_longlong(r2) < rc2b) {
+          const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+          Fx = fma(g, dx, Fx);
+          Fy = fma(g, dy, Fy);
+          Fz = fma(g, dz, Fz);
+        }
       }
-      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-      if (__double_as_longlong(r2) < rc2b) {
-        const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
-        Fx = fma(g, dx, Fx);
-        Fy = fma(g, dy, Fy);
-        Fz = fma(g, dz, Fz);
+    }
+  } else {  // every lane of the warp takes part (inactive ones with an empty list)
+    const int cnt = t.act ? list_count(a, t.sys, t.s, P.kmax) : 0;
+    const uint4* lp4 = (const uint4*)(a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0));
+    const int4* qs = a.xq[cur] + P.p_off;
+    const double4_32a* xs = a.x[cur] + P.p_off;
+    const int4 qi = t.act ? qs[t.local] : make_int4(0, 0, 0, 0);
+    const long long rc2b = __double_as_longlong(P.rc2);
+    const float rc2q = P.rc2q_hi;
+    const double c2x8 = 8.0 * P.c2, L = P.L;
+    const uint32_t self = (uint32_t)t.local;
+    uint32_t* qme = &qbuf[0][threadIdx.x];
+    int k = 0;                 // next listed partner to classify
+    unsigned head = 0u, tail = 0u;
+    while (true) {
+      const unsigned qn = tail - head;
+      const bool left = k < cnt;
+      const unsigned has = __ballot_sync(kFull, qn > 0u);
+      const unsigned busy = __ballot_sync(kFull, qn > 0u || left);
+      if (busy == 0u) break;
+      const unsigned room = __ballot_sync(kFull, left && qn <= (unsigned)(kQueue64 - 4));
+      if (has == busy || room == 0u) {
+        // FP64 round: each thread with a queued pair takes the next one
+        if (qn > 0u) {
+          const uint32_t e = qme[(head & (kQueue64 - 1)) * BLOCK];
+          ++head;
+          const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, self)];
+          double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+          const unsigned code = e >> kIdxBits;
+          if (code) {
+            dx = apply_image(dx, code & 3u, L);
+            dy = apply_image(dy, (code >> 2) & 3u, L);
+            dz = apply_image(dz, (code >> 4) & 3u, L);
+          }
+          const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+          if (__double_as_longlong(r2) < rc2b) {
+            const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+            Fx = fma(g, dx, Fx);
+            Fy = fma(g, dy, Fy);
+            Fz = fma(g, dz, Fz);
+          }
+        }
+      } else if ((room >> lane) & 1u) {
+        // classification of the next four listed partners (no FP64 instruction)
+        const uint4 w = __ldg(lp4 + (int64_t)(k >> 2) * kTile);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const bool ok = k + m < cnt;
+          const int4 qj = qs[ok ? partner_slot(a, t.sys, ws[m], P.n, self) : self];
+          const float ax = (float)wrapped_diff(qj.x, qi.x);
+          const float ay = (float)wrapped_diff(qj.y, qi.y);
+          const float az = (float)wrapped_diff(qj.z, qi.z);
+          if (ok && fmaf(az, az, fmaf(ay, ay, ax * ax)) < rc2q) {
+            qme[(tail & (kQueue64 - 1)) * BLOCK] = ws[m];
+            ++tail;
+          }
+        }
+        k += 4;
       }
     }
   }
@@ -1694,25 +1775,32 @@ void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream
     default: launch_build_list_v<0>(a, cur, tu.list_block, s); break;
   }
 }
-template <int MODE>
+template <int MODE, bool QUEUE>
 static void launch_step_fp64_m(const DevArrays& a, int cur, double ka, double kb, int flags, int block,
                                cudaStream_t s) {
   switch (block) {
-    case 64: k_step_fp64<64, MODE><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, ka, kb, flags); break;
-    case 256: k_step_fp64<256, MODE><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, ka, kb, flags); break;
-    default: k_step_fp64<128, MODE><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, ka, kb, flags); break;
+    case 64: k_step_fp64<64, MODE, QUEUE><<<blocks_of(a, 64), 64, 0, s>>>(a, cur, ka, kb, flags); break;
+    case 256: k_step_fp64<256, MODE, QUEUE><<<blocks_of(a, 256), 256, 0, s>>>(a, cur, ka, kb, flags); break;
+    default: k_step_fp64<128, MODE, QUEUE><<<blocks_of(a, 128), 128, 0, s>>>(a, cur, ka, kb, flags); break;
+  }
+}
+
+template <bool QUEUE>
+static void launch_step_fp64_q(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
+                               int mode, cudaStream_t s) {
+  switch (mode) {
+    case 1: launch_step_fp64_m<1, QUEUE>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 2: launch_step_fp64_m<2, QUEUE>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 3: launch_step_fp64_m<3, QUEUE>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    case 4: launch_step_fp64_m<4, QUEUE>(a, cur, ka, kb, flags, tu.step_block, s); break;
+    default: launch_step_fp64_m<0, QUEUE>(a, cur, ka, kb, flags, tu.step_block, s); break;
   }
 }
 
 void launch_step_fp64(const DevArrays& a, int cur, double ka, double kb, int flags, const Tuning& tu,
                       int mode, cudaStream_t s) {
-  switch (mode) {
-    case 1: launch_step_fp64_m<1>(a, cur, ka, kb, flags, tu.step_block, s); break;
-    case 2: launch_step_fp64_m<2>(a, cur, ka, kb, flags, tu.step_block, s); break;
-    case 3: launch_step_fp64_m<3>(a, cur, ka, kb, flags, tu.step_block, s); break;
-    case 4: launch_step_fp64_m<4>(a, cur, ka, kb, flags, tu.step_block, s); break;
-    default: launch_step_fp64_m<0>(a, cur, ka, kb, flags, tu.step_block, s); break;
-  }
+  if (tu.fp64_queue) launch_step_fp64_q<true>(a, cur, ka, kb, flags, tu, mode, s);
+  else launch_step_fp64_q<false>(a, cur, ka, kb, flags, tu, mode, s);
 }
 template <int MODE>
 static void launch_force_half_fp64_m(const DevArrays& a, int cur, int flags, int block, cudaStream_t s) {

@@ -40,9 +40,10 @@ MD_TUNE_LIST_BLOCK = 2
 MD_TUNE_LIST_VARIANT = 3
 MD_TUNE_STEP_HINT = 4
 MD_TUNE_GRAPH = 5
+MD_TUNE_FP64_QUEUE = 6
 TUNING_KEYS = {"step_block": MD_TUNE_STEP_BLOCK, "step_groups": MD_TUNE_STEP_GROUPS,
                "list_block": MD_TUNE_LIST_BLOCK, "list_variant": MD_TUNE_LIST_VARIANT,
-               "step_hint": MD_TUNE_STEP_HINT, "graph": MD_TUNE_GRAPH}
+               "step_hint": MD_TUNE_STEP_HINT, "graph": MD_TUNE_GRAPH, "fp64_queue": MD_TUNE_FP64_QUEUE}
 
 _ERRNAMES = {v: k for k, v in dict(MD_ERR_ARG=-1, MD_ERR_OOM=-2, MD_ERR_LIST_OVERFLOW=-3,
                                    MD_ERR_NONFINITE=-4, MD_ERR_TIMEOUT=-5, MD_ERR_CUDA=-6,

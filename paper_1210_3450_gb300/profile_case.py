@@ -34,6 +34,7 @@ def main(argv=None):
     p.add_argument("--list-block", type=int, default=None)
     p.add_argument("--step-hint", type=int, default=None)
     p.add_argument("--list-variant", type=int, default=None)
+    p.add_argument("--fp64-queue", type=int, default=None)
     p.add_argument("--autotune", action="store_true")
     p.add_argument("--half", action="store_true", help="half pair list with Newton's third law")
     a = p.parse_args(argv)
@@ -49,7 +50,7 @@ def main(argv=None):
     with LJSystem(box, n, a.rc, a.skin, mode) as s:
         tun = {k: val for k, val in dict(step_block=a.step_block, step_groups=a.step_groups,
                                          list_block=a.list_block, step_hint=a.step_hint,
-                                         list_variant=a.list_variant).items()
+                                         list_variant=a.list_variant, fp64_queue=a.fp64_queue).items()
                if val is not None}
         if tun:
             s.set_tuning(**tun)

@@ -16,7 +16,9 @@ def test_tuning_does_not_change_results(ljmd, precision):
     for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=0, step_hint=0),
                 dict(step_block=64, step_groups=2, list_block=256, list_variant=3, step_hint=1),
                 dict(step_block=256, step_groups=2, list_block=64, list_variant=4, step_hint=1),
-                dict(step_block=128, step_groups=1, list_block=128, list_variant=2, step_hint=1)]:
+                dict(step_block=128, step_groups=1, list_block=128, list_variant=2, step_hint=1),
+                dict(step_block=128, step_groups=2, list_block=256, list_variant=1, step_hint=1,
+                     fp64_queue=0)]:
         with ljmd.LJSystem(box, 3000, 2.5, 0.3, precision) as s:
             s.set_tuning(**tun)
             got = s.get_tuning()
