@@ -241,12 +241,14 @@ MD_API int md_get_timing(md_ctx* ctx, double* out8);
  *   x_dev  N*3 float64 positions on the current device (any real values: wrapped
  *          into [0, box_L) internally), read only;
  *   f_dev  N*3 float64 output on the current device: F_i = sum over j != i with
- *          minimum-image r < rc of (24 r^-8 - 48 r^-14 + 8 c2)(x_j - x_i) (Eq. 1),
- *          the same forces as md_forces (no pair list; cells of side >= rc);
+ *          minimum-image r < rc of (24 r^-8 - 48 r^-14 + 8 c2)(x_j - x_i), the same
+ *          pair force as md_forces (no pair list; cells of side >= rc, the particles
+ *          of a cell taken in caller order, so the same positions give the same
+ *          forces bit for bit from call to call);
  *   stream cudaStream_t as void* (NULL = legacy default stream); the call only
  *          enqueues work on it and returns without synchronising.
  * Limits: 1 <= N <= 65536, rc > 0, 2 rc < box_L <= 10000; larger N returns MD_ERR_ARG.
- * Working memory is one fixed 2.75 MiB device array inside the library (every GPU
+ * Working memory is one fixed 3.0 MiB device array inside the library (every GPU
  * that loads the library holds it until the process exits); nothing is allocated.
  * The first call on a device looks up that array's device address with that device
  * current; make this first call before any stream capture. All calls share the one

@@ -9,7 +9,8 @@
 // working memory in one fixed file-scope device array instead of allocating it.
 //
 // The working memory (cell counters, cell starts, per-particle cells, the
-// cell-sorted copy of the positions) lives in g_noalloc_scratch below; every GPU
+// scattered caller indices, the cell-sorted copy of the positions) lives in
+// g_noalloc_scratch below; every GPU
 // that loads this library holds that array until the process exits. Host code
 // cannot use the symbol g_noalloc_scratch as a device address (it names a host
 // stand-in), so the device address is looked up with cudaGetSymbolAddress, once
@@ -36,8 +37,9 @@ constexpr int kNaMaxDevices = 64;
 constexpr size_t kOffCount = 0;                                          // int[kNaMaxCells]
 constexpr size_t kOffStart = kOffCount + 4 * kNaMaxCells;                // int[kNaMaxCells + 1]
 constexpr size_t kOffCell = kOffStart + 4 * (kNaMaxCells + 256);         // int[kNaMaxN]
-constexpr size_t kOffPos = kOffCell + 4 * kNaMaxN;                       // double4_32a[kNaMaxN]
-constexpr size_t kScratchBytes = kOffPos + 32 * kNaMaxN;                 // 2.75 MiB
+constexpr size_t kOffIdx = kOffCell + 4 * kNaMaxN;                       // int[kNaMaxN]
+constexpr size_t kOffPos = kOffIdx + 4 * kNaMaxN;                        // double4_32a[kNaMaxN]
+constexpr size_t kScratchBytes = kOffPos + 32 * kNaMaxN;                 // 3.0 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -50,7 +52,8 @@ struct NaScratch {
   int* count;
   int* start;
   int* cell;
-  double4_32a* pos;  // wrapped positions in cell order; w = caller index (as double)
+  int* idx;          // caller indices scattered into cell order (arbitrary within a cell)
+  double4_32a* pos;  // wrapped positions in cell order, by caller index within a cell; w = caller index
 };
 
 __device__ __forceinline__ NaScratch na_view(unsigned char* base) {
@@ -58,6 +61,7 @@ __device__ __forceinline__ NaScratch na_view(unsigned char* base) {
   s.count = (int*)(base + kOffCount);
   s.start = (int*)(base + kOffStart);
   s.cell = (int*)(base + kOffCell);
+  s.idx = (int*)(base + kOffIdx);
   s.pos = (double4_32a*)(base + kOffPos);
   return s;
 }
@@ -116,14 +120,29 @@ __global__ void __launch_bounds__(1024) k_na_scan(unsigned char* base, int ncell
   if (tid == 0) s.start[ncell] = carry;
 }
 
-__global__ void k_na_scatter(unsigned char* base, NaParams p, const double* __restrict__ x) {
+// Caller indices into their cells' ranges, in arrival order.
+__global__ void k_na_scatter(unsigned char* base, NaParams p) {
   NaScratch s = na_view(base);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
   const int c = s.cell[i];
-  const int q = s.start[c] + atomicAdd(&s.count[c], 1);
-  s.pos[q] = make_double4_32a(wrap_full(x[3 * i + 0], p.L), wrap_full(x[3 * i + 1], p.L),
-                              wrap_full(x[3 * i + 2], p.L), (double)i);
+  s.idx[s.start[c] + atomicAdd(&s.count[c], 1)] = i;
+}
+
+// Each particle's place in its cell is the number of the cell's particles with a
+// smaller caller index, so the cell-sorted positions, and with them the order of
+// every force sum, do not depend on the order of the atomics above: the same
+// positions give the same forces bit for bit.
+__global__ void k_na_rank(unsigned char* base, NaParams p, const double* __restrict__ x) {
+  NaScratch s = na_view(base);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int c = s.cell[i];
+  const int lo = s.start[c], hi = s.start[c + 1];
+  int rank = 0;
+  for (int q = lo; q < hi; ++q) rank += s.idx[q] < i ? 1 : 0;
+  s.pos[lo + rank] = make_double4_32a(wrap_full(x[3 * i + 0], p.L), wrap_full(x[3 * i + 1], p.L),
+                                      wrap_full(x[3 * i + 2], p.L), (double)i);
 }
 
 // Force on caller particle i from every j in the 27 neighbour cells (or from all
@@ -238,9 +257,13 @@ extern "C" int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, d
   NaParams p;
   p.L = box_L;
   p.n = (int)N;
-  int nc = (int)std::floor(box_L / rc);
+  // cells per axis, floor(L / rc), clamped in double before the conversion (L / rc
+  // can exceed the int range); lowered by one where rounding could make a cell
+  // narrower than rc, and at most 32 (coarser cells stay valid: side > rc)
+  const double q = std::floor(box_L / rc);
+  int nc = q > 33.0 ? 33 : (int)q;
   if (nc >= 1 && box_L / nc < rc * (1.0 + 1e-9)) nc -= 1;
-  if (nc > 32) nc = 32;  // coarser cells stay valid (side > rc)
+  if (nc > 32) nc = 32;
   p.nc = nc >= 3 ? nc : 1;
   p.inv_cs = (double)p.nc / box_L;
   p.rc2 = rc * rc;
@@ -252,7 +275,8 @@ extern "C" int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, d
   k_na_clear<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(base, ncell);
   k_na_bin<<<blocks, 256, 0, s>>>(base, p, x_dev);
   k_na_scan<<<1, 1024, 0, s>>>(base, ncell);
-  k_na_scatter<<<blocks, 256, 0, s>>>(base, p, x_dev);
+  k_na_scatter<<<blocks, 256, 0, s>>>(base, p);
+  k_na_rank<<<blocks, 256, 0, s>>>(base, p, x_dev);
   k_na_force<<<blocks, 256, 0, s>>>(base, p, x_dev, f_dev);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
