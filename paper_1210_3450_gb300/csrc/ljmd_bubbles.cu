@@ -30,12 +30,25 @@ __global__ void k_gas_init(const uint32_t* counts, int64_t ncell, double gas_cou
   parent[c] = (double)counts[c] < gas_count ? (int32_t)c : -1;
 }
 
+// parent[] is read and written by threads on every SM while the union runs, so
+// its accesses are relaxed atomics at GPU scope: a plain load may be served from
+// this SM's L1 and keep returning a root that another SM has linked meanwhile
+// (each compare-and-swap would then fail until the retry bound).
+__device__ __forceinline__ int32_t ld_parent(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_parent(int32_t* p, int32_t v) {
+  asm volatile("st.relaxed.gpu.s32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
 // Root of c (parent chains only ever point to smaller indices).
 __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t c) {
-  int32_t p = parent[c];
+  int32_t p = ld_parent(parent + c);
   while (p != c) {
-    const int32_t g = parent[p];
-    if (g != p) parent[c] = g;  // path halving (benign race: g is an ancestor)
+    const int32_t g = ld_parent(parent + p);
+    if (g != p) st_parent(parent + c, g);  // path halving (benign race: g is an ancestor)
     c = p;
     p = g;
   }
@@ -71,7 +84,7 @@ __global__ void k_gas_union(int32_t* parent, int ns, int* err) {
                          cx + (int64_t)ns * (cy + (int64_t)ns * ((cz + 1) % ns))};
 #pragma unroll
   for (int q = 0; q < 3; ++q)
-    if (parent[nb[q]] >= 0) uf_union(parent, (int32_t)c, (int32_t)nb[q], err);
+    if (ld_parent(parent + nb[q]) >= 0) uf_union(parent, (int32_t)c, (int32_t)nb[q], err);
 }
 
 // Final labels (roots) and cluster sizes.

@@ -64,3 +64,39 @@ def test_bubbles_in_an_expanded_liquid(ljmd, oracle):
     np.testing.assert_array_equal(g["counts"], np.minimum(ref["counts"], 255).astype(np.uint8))
     assert g["n_bubbles"] == ref["n_bubbles"]
     np.testing.assert_array_equal(g["sizes"], ref["sizes"])
+
+
+def _mask_particles(gas, ns, side=3.0):
+    """Six particles in every liquid subcell of an ns^3 lattice of side `side`
+    (count 6 >= 0.2 * 27), none in the gas subcells; pairs no closer than 1.5."""
+    off = np.array([[0.5, 0.5, 0.5], [2.0, 0.5, 0.5], [0.5, 2.0, 0.5], [0.5, 0.5, 2.0],
+                    [2.0, 2.0, 0.5], [2.0, 0.5, 2.0]])
+    liquid = np.flatnonzero(~gas)
+    ijk = np.stack([liquid % ns, (liquid // ns) % ns, liquid // (ns * ns)], axis=1).astype(np.float64)
+    return (ijk[:, None, :] * side + off[None]).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("gas_fraction", [0.2, 0.35])
+def test_bubbles_on_a_100_cubed_lattice(ljmd, oracle, gas_fraction):
+    """The subcell lattice of the cavitation configuration (100^3 subcells of side
+    3): a random gas mask at 20 % (many small clusters) and at 35 % (above the
+    site-percolation threshold of the simple cubic lattice, 0.31: one cluster spans
+    the box, so union-find chains cross every SM). Cluster count and sizes equal
+    the oracle's flood fill, and the union-find finishes within its retry bound
+    (md_bubbles reports an overrun as an error)."""
+    ns = 100
+    rng = np.random.default_rng(731 + int(gas_fraction * 100))
+    gas = rng.random(ns ** 3) < gas_fraction
+    x = _mask_particles(gas, ns)
+    box = 3.0 * ns
+    with ljmd.LJSystem(box, len(x), 3.0, 0.3, ljmd.MD_FP32_FORCE) as s:
+        s.set_state(x, np.zeros_like(x))
+        g = s.bubbles(3.0, 0.2)
+    k, label = oracle.clusters(gas, ns)
+    sizes = np.sort(np.bincount(label[label >= 0])[np.bincount(label[label >= 0]) > 0])[::-1]
+    assert g["ns"] == ns
+    np.testing.assert_array_equal(g["counts"], np.where(gas, 0, 6).astype(np.uint8))
+    assert g["n_bubbles"] == k
+    np.testing.assert_array_equal(g["sizes"], sizes)
+    if gas_fraction > 0.32:
+        assert sizes[0] > 0.5 * gas.sum()   # the spanning cluster
