@@ -24,10 +24,7 @@ import argparse
 import hashlib
 import json
 import os
-import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -36,6 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s (FP32-force vs FP64) + roofline %; p50/p99 batched MD latency"
 UNIT = "particle-steps/s"
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (vector and tensor), recipe table
+
+# Compulsory bytes per particle-step of the fused FP32 force + integration kernel
+# (k_step_fp32), by name; the list adds 4 bytes per listed partner.
+FP32_STEP_BYTES = {
+    "partner_shadows_once": 16,   # every particle's 16-byte shadow is gathered at least once
+    "position_read": 32,          # own FP64 position (double4)
+    "position_write": 32,         # drifted position into the other buffer
+    "velocity_read": 32,
+    "velocity_write": 32,
+    "shadow_write": 16,           # fixed-point shadow of the drifted position
+    "reference_shadow_read": 16,  # shadow at the last list build (validity check)
+    "list_length": 4,
+}
 
 
 def parse_args():
@@ -46,7 +56,11 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--skip-cpu-baseline", action="store_true")
     p.add_argument("--skip-batched", action="store_true", help="no batched-replica / serving sub-results")
+    p.add_argument("--skip-cavitation", action="store_true", help="no cavitation-run sub-result")
+    p.add_argument("--skip-serve-spec", action="store_true",
+                   help="no as-specified serving run (200 requests/s for 60 s)")
     p.add_argument("--serve-seconds", type=float, default=20.0)
+    p.add_argument("--cavitation-steps", type=int, default=2000)
     return p.parse_args()
 
 
@@ -62,64 +76,6 @@ def workload_config():
         "parallelism": "replicas",
     }
     return cfg, desc
-
-
-# ------------------------------------------------------------------ clocks
-
-class ClockSampler:
-    """nvidia-smi samples every 200 ms during the timed regions."""
-
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
-        self.proc = None
-        self.path = None
-        self.windows = []
-
-    def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
-        try:
-            self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.idx)], stdout=self.fh, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
-
-    def mark(self, begin: bool):
-        t = time.time()
-        if begin:
-            self.windows.append([t, None])
-        else:
-            self.windows[-1][1] = t
-
-    def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.fh.close()
-        rows = []
-        with open(self.path) as fh:
-            for line in fh:
-                parts = [q.strip() for q in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(rows), "reasons": reasons}
 
 
 # ------------------------------------------------------------------ helpers
@@ -223,31 +179,60 @@ def e2e_run(ljmd, cfg, precision, steps):
     return dict(seconds=t1 - t0, h2d=2 * 8 * 3 * cfg.n, d2h=2 * 8 * 3 * cfg.n + 5 * 8, obs=o)
 
 
-def cpu_baseline(cfg, budget_s=20.0):
-    """The oracle (single thread, as it stands) on a bounded sample of the workload:
-    an FCC m^3 x 4 block at the same density, temperature, cutoff, skin and dt;
-    per-step time = (t(run of 1 + k steps) - t(run of 1 step)) / k, so the list
-    build at the start of each run is excluded once."""
+_SAMPLE_M = 24  # the oracle's bounded sample: an FCC 24^3 x 4 block (55,296 particles)
+
+
+def _oracle_sample_rate(args):
+    """Particle-steps/s of the oracle on the bounded sample (run in one process):
+    per-step time = (t(1 + k steps) - t(1 step)) / k, so the list build at the
+    start of each run is excluded once."""
+    rho, temperature, rc, skin, dt, k = args
     import lj_inputs as li
     import oracle
-    m = 24
-    n = 4 * m ** 3
-    box = li.box_length(n, cfg.rho)
+    n = 4 * _SAMPLE_M ** 3
+    box = li.box_length(n, rho)
     x = li.fcc_positions(n, box)
-    v = li.maxwell_boltzmann(n, cfg.temperature, 1002)
+    v = li.maxwell_boltzmann(n, temperature, 1002)
     t = time.perf_counter()
-    oracle.run(x, v, box, cfg.rc, cfg.skin, 1, cfg.dt)
+    oracle.run(x, v, box, rc, skin, 1, dt)
     t1 = time.perf_counter() - t
-    k = max(2, int(budget_s / max(t1, 1e-3)))
-    k = min(k, 40)
     t = time.perf_counter()
-    oracle.run(x, v, box, cfg.rc, cfg.skin, 1 + k, cfg.dt)
+    oracle.run(x, v, box, rc, skin, 1 + k, dt)
     tk = time.perf_counter() - t
-    per_step = max((tk - t1) / k, 1e-9)
-    return {"value": n / per_step, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FCC {m}^3x4 = {n} particles at rho={cfg.rho}, T={cfg.temperature}, "
-                      f"rc={cfg.rc}, skin={cfg.skin}, dt={cfg.dt}; {k} steps timed "
-                      f"(initial list build excluded); single thread"}
+    return n * k / max(tk - t1, 1e-9), tk + t1
+
+
+def cpu_baseline(cfg, budget_s=15.0):
+    """The oracle as it stands on a bounded sample of the workload (an FCC 24^3 x 4
+    block at the same density, temperature, cutoff, skin and dt): one thread, and
+    all host cores as independent oracle processes on the same sample (the oracle
+    is single-threaded; started with spawn, its results are the same per process)."""
+    import multiprocessing as mp
+    n = 4 * _SAMPLE_M ** 3
+    rate1, _ = _oracle_sample_rate((cfg.rho, cfg.temperature, cfg.rc, cfg.skin, cfg.dt, 2))
+    k = int(max(2, min(40, budget_s * rate1 / n)))
+    rate1, _ = _oracle_sample_rate((cfg.rho, cfg.temperature, cfg.rc, cfg.skin, cfg.dt, k))
+    cores = os.cpu_count() or 1
+    sample = (f"FCC {_SAMPLE_M}^3x4 = {n} particles at rho={cfg.rho}, T={cfg.temperature}, "
+              f"rc={cfg.rc}, skin={cfg.skin}, dt={cfg.dt}; {k} steps timed (initial list build "
+              f"excluded)")
+    out = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + "; single thread"}
+    kall = max(2, k // 2)
+    try:
+        ctx = mp.get_context("spawn")
+        t = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_sample_rate, [(cfg.rho, cfg.temperature, cfg.rc, cfg.skin, cfg.dt, kall)] * cores)
+        wall = time.perf_counter() - t
+        # whole-job throughput: particle-steps of all processes over the slowest one's
+        # timed steps (the per-process rates are summed over a shared wall window)
+        out["all_cores"] = {"value": sum(r[0] for r in res), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample.replace(f"{k} steps", f"{kall} steps")
+                                      + f"; {cores} independent single-thread oracle processes at once",
+                            "wall_s": round(wall, 2)}
+    except Exception as e:  # the single-thread figure stands on its own
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def replica_totals(dist, seconds: float, units: float, device: str = "cpu") -> tuple[float, float]:
@@ -264,6 +249,26 @@ def replica_totals(dist, seconds: float, units: float, device: str = "cpu") -> t
     return float(t.item()), float(u.item())
 
 
+def cavitation_leg(steps: int) -> dict:
+    """The cavitation-shaped run (16,384,000 particles at rho 0.70, T 0.90, rc 3.0):
+    Nose-Hoover equilibration, uniform expansion by 1.05 per axis, then `steps` NVE
+    steps in graph-captured chunks (timed), with pressure and bubbles at the end."""
+    from paper_1210_3450_gb300 import workloads
+    r = workloads.cavitation(cells=160, equil_steps=2000, steps=steps, obs_every=steps)
+    last = r["series"][-1]
+    return {"workload": r["workload"], "value": round(r["value"], 1), "unit": r["unit"],
+            "ms_per_step": round(r["ms_per_step"], 4), "steps": r["steps"], "list_builds": r["list_builds"],
+            "steps_per_build": round(r["steps_per_build"], 2),
+            "kernel_ms_per_step": round(r["kernel_ms_per_step"], 4),
+            "list_build_ms": round(r["list_build_ms_per_launch"], 4),
+            "equilibration": {k: (round(v, 5) if isinstance(v, float) else v)
+                              for k, v in r["equilibration"].items()},
+            "final": {"pressure": round(last["pressure"], 6), "temperature": round(last["temperature"], 6),
+                      "bubbles": last["bubbles"], "largest_bubble_subcells": last["largest_bubble_subcells"],
+                      "gas_subcells": last["gas_subcells"]},
+            "note": "NVE phase timed with CUDA events; observables and bubbles outside the timed chunks"}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -278,12 +283,13 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1210_3450_gb300.ljmd as ljmd
+    from paper_1210_3450_gb300.clocks import ClockSampler
     cfg, desc = workload_config()
     stream = torch.cuda.Stream()
     clocks = ClockSampler(local)
     clocks.start()
     r32 = time_form(ljmd, cfg, ljmd.MD_FP32_FORCE, args.steps, args.warmup, stream, clocks, dist)
-    r64_steps = max(args.steps // 4, 10)
+    r64_steps = max(args.steps // 10, 100)
     r64 = time_form(ljmd, cfg, ljmd.MD_FP64, r64_steps, max(args.warmup // 4, 3), stream, clocks, dist)
     ck = clocks.stop()
 
@@ -297,12 +303,22 @@ def run_ours(args):
     e2e_sec, e2e_units = replica_totals(dist, e2e["seconds"], float(cfg.n * args.steps), "cuda")
     e2e_val = e2e_units / e2e_sec
 
-    batched = serve = None
-    if not args.skip_batched and rank == 0:
+    # the other workloads and the baselines: one GPU only (under torchrun every rank
+    # runs the headline replica alone)
+    extras = world == 1 and rank == 0
+    batched = serve = serve_spec = cav = rates = None
+    if extras:
+        rates = {"fp64_dfma_per_s": ljmd.probe_fma_rate(0, 100_000),
+                 "fp32_ffma_per_s": ljmd.probe_fma_rate(1, 5_000_000)}
+    if extras and not args.skip_batched:
         from paper_1210_3450_gb300 import workloads
-        batched = workloads.batched(count=256, steps=500, warmup=10)
+        batched = workloads.batched(count=256, steps=1000, warmup=10)
         rate = 0.8 * batched["value"] / workloads.mean_request_work()
         serve = workloads.serve_run(rate, args.serve_seconds, budget_gb=100.0)
+        if not args.skip_serve_spec:
+            serve_spec = workloads.serve_run(200.0, 60.0, budget_gb=100.0, drain_limit=60.0)
+    if extras and not args.skip_cavitation:
+        cav = cavitation_leg(args.cavitation_steps)
 
     if rank != 0:
         if dist:
@@ -312,32 +328,44 @@ def run_ours(args):
 
     hbm_peak, peak_src = load_peaks()
     n = cfg.n
-    # fused FP32 step kernel: algorithmic bytes per particle-step
+    # fused FP32 step kernel: compulsory bytes per particle-step, by name
     lp = r32["listed"] / n
-    bytes_pp = 4.0 * lp + 208.0
+    breakdown = {"list_words": round(4.0 * lp, 1), **FP32_STEP_BYTES}
+    bytes_pp = sum(breakdown.values())
     t32 = r32["timing"]
     k_ms = t32["step_ms"] / max(t32["step_launches"], 1)
     achieved = bytes_pp * n / (k_ms / 1e3) / 1e9
     traffic = profiled_traffic("k_step_fp32", n)
-    roof = {"bound": "hbm", "kernel": "k_step<fp32> (fused force + velocity Verlet)",
+    roof = {"bound": "hbm", "kernel": "k_step_fp32 (fused FP32 pair force + velocity Verlet)",
             "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-            "algorithmic_bytes_per_particle_step": round(bytes_pp, 1),
+            "algorithmic_bytes_per_particle_step": round(bytes_pp, 1), "bytes_breakdown": breakdown,
+            "achieved_dram": round(traffic / (k_ms / 1e3) / 1e9, 1) if traffic else None,
+            "frac_dram": round(traffic / (k_ms / 1e3) / 1e9 / hbm_peak, 4) if traffic else None,
             "avg_launch_ms": round(k_ms, 4),
             "avg_launch_ms_source": "CUDA events around each launch (host-driven pass of the same run)"}
-    # FP64 step kernel: FP64-pipe bound (FMA = 2 flops)
+    # FP64 step kernel: FP64-pipe bound; flops as the method needs them: the
+    # separation and r^2 of every listed pair (10, an FMA counted as 2) and the
+    # force of every pair inside rc (16)
     t64 = r64["timing"]
     k64 = t64["step_ms"] / max(t64["step_launches"], 1)
     lp64 = r64["listed"] / n
     in64 = r64["inside"] / n
-    flops_pp = 8.0 * lp64 + 19.0 * in64 + 26.0
+    flops_pp = 10.0 * lp64 + 16.0 * in64
     ach64 = flops_pp * n / (k64 / 1e3) / 1e12
-    roof64 = {"bound": "alu", "kernel": "k_step<fp64>", "achieved": round(ach64, 4),
-              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach64 / FP64_PEAK_TFLOPS, 4),
+    roof64 = {"bound": "alu", "kernel": "k_step_fp64 (classified, queued FP64 pair force + velocity Verlet)",
+              "achieved": round(ach64, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "frac": round(ach64 / FP64_PEAK_TFLOPS, 4),
               "traffic": profiled_traffic("k_step_fp64", n),
-              "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s); probe-measured DFMA rate 1.05 TFLOP/s",
-              "algorithmic_flops_per_particle_step": round(flops_pp, 1), "avg_launch_ms": round(k64, 4)}
+              "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s, recipe table)",
+              "algorithmic_flops_per_particle_step": round(flops_pp, 1),
+              "flop_count": "10 per listed pair (separation, r^2) + 16 per pair inside rc (force, accumulation)",
+              "avg_launch_ms": round(k64, 4)}
+    if rates:
+        meas = 2.0 * rates["fp64_dfma_per_s"] / 1e12
+        roof64.update(peak_measured=round(meas, 4), frac_measured=round(ach64 / meas, 4),
+                      peak_measured_source="md_probe_fma_rate: DFMA chains on every SM, this run")
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32 / args.steps, 5),
@@ -361,13 +389,26 @@ def run_ours(args):
                          "memory) + observables through the C ABI, wall clock")},
         "clocks": ck,
     }
+    if rates:
+        line["pipe_rates"] = {"fp64_tflops": round(2.0 * rates["fp64_dfma_per_s"] / 1e12, 4),
+                              "fp32_tflops": round(2.0 * rates["fp32_ffma_per_s"] / 1e12, 2),
+                              "source": "md_probe_fma_rate (FMA = 2 flops), this run"}
     if batched:
         line["batched"] = {k: batched[k] for k in ("workload", "value", "unit", "ms_per_step", "steps",
-                                                    "list_builds", "launches_per_step")}
+                                                    "list_builds", "launches_per_step", "autotuned")}
     if serve:
         line["serve"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in serve.items()}
         line["serve"]["note"] = ("Poisson arrivals at 80% of the batched capacity, N log-uniform "
                                  "[1e3, 1e6], steps [1e3, 1e4]; latency includes queueing")
+    if serve_spec:
+        line["serve_as_specified"] = {k: (round(v, 4) if isinstance(v, float) else v)
+                                      for k, v in serve_spec.items()}
+        line["serve_as_specified"]["note"] = (
+            "Poisson arrivals at 200 requests/s for 60 s (offered load about 40x one GPU); the run stops "
+            "60 s after the last arrival; latency percentiles over the completed requests, unfinished "
+            "ones counted and their remaining work projected at the measured rate")
+    if cav:
+        line["cavitation"] = cav
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg)
     print(json.dumps(line), flush=True)

@@ -257,6 +257,17 @@ MD_API int md_get_timing(md_ctx* ctx, double* out8);
 MD_API int md_forces_noalloc(const double* x_dev, int64_t N, double box_L, double rc,
                              double* f_dev, void* stream);
 
+/* Measurement utility, not part of the paper's method: the fused multiply-add
+ * throughput of one arithmetic pipe of the current device, the denominator of the
+ * FP64 force kernel's roofline (that kernel is bound by the FP64 pipe, not HBM).
+ *   kind       0: FP64 (DFMA), 1: FP32 (FFMA)
+ *   iters      iterations of eight independent chains per thread (64 warps per SM);
+ *              about 1e5 (FP64) or 5e6 (FP32) run for a few hundred milliseconds
+ *   fma_per_s  output: thread-level FMA instructions per second (flops = 2 x)
+ * Launches on the legacy default stream and synchronises it. Errors: MD_ERR_ARG,
+ * MD_ERR_CUDA. */
+MD_API int md_probe_fma_rate(int kind, int64_t iters, double* fma_per_s);
+
 /* Launch shapes of the hot kernels (results do not depend on them, only speed):
  *   MD_TUNE_STEP_BLOCK   threads per block of the force + integration kernel: 64, 128, 256
  *   MD_TUNE_STEP_GROUPS  FP32-force partners loaded per iteration, in groups of 4: 1, 2

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libljmd.so")
-SOURCES = ["ljmd_kernels.cu", "ljmd_engine.cu", "ljmd_capi.cu", "ljmd_noalloc.cu", "ljmd_bubbles.cu"]
+SOURCES = ["ljmd_kernels.cu", "ljmd_engine.cu", "ljmd_capi.cu", "ljmd_noalloc.cu", "ljmd_bubbles.cu",
+           "ljmd_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-fvisibility=hidden", "-I", os.path.join(ROOT, "include")]

@@ -96,6 +96,7 @@ SIGNATURES = {
     "md_set_timing": (C.c_int, [_P, C.c_int]),
     "md_get_timing": (C.c_int, [_P, _PD]),
     "md_forces_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, C.c_double, _P, _P]),
+    "md_probe_fma_rate": (C.c_int, [C.c_int, C.c_int64, _PD]),
     "md_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "md_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "md_batch_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
@@ -607,6 +608,14 @@ def forces_noalloc(x, box: float, rc: float, f, stream=None):
     n = x.numel() // 3
     _check(load_library().md_forces_noalloc(_dev_ptr(x, n), n, float(box), float(rc),
                                             _dev_ptr(f, n), _stream_ptr(stream)))
+
+
+def probe_fma_rate(kind: int, iters: int) -> float:
+    """md_probe_fma_rate: FMA instructions per second of the FP64 (kind 0) or FP32
+    (kind 1) pipe of the current device."""
+    out = C.c_double()
+    _check(load_library().md_probe_fma_rate(int(kind), int(iters), C.byref(out)))
+    return out.value
 
 
 def version() -> str:

@@ -46,10 +46,14 @@ def _cuda_time(fn, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-def batched(count=256, steps=2000, warmup=20, precision=1, seed=1004) -> dict:
+def batched(count=256, steps=2000, warmup=20, precision=1, seed=1004, tune=True,
+            tune_cache: str | None = None) -> dict:
+    """The replica batch; with tune=True the autotuner picks the launch shapes on
+    the batch itself first (or takes them from its keyed cache) and the chosen
+    tuning is part of the result."""
     import torch
     import lj_inputs as li
-    from . import ljmd
+    from . import autotune, ljmd
     syss = li.batch_systems(count=count, seed=seed)
     n_tot = sum(c.n for c in syss)
     b = ljmd.LJBatch(systems=[(c.n, c.box, c.rc, c.skin) for c in syss], precision=precision)
@@ -57,6 +61,12 @@ def batched(count=256, steps=2000, warmup=20, precision=1, seed=1004) -> dict:
         b.set_state(k, c.x, c.v)
     dts = [c.dt for c in syss]
     stream = torch.cuda.Stream()
+    tuned = None
+    if tune:
+        key = autotune.shape_key(precision, n_tot, sum(c.rho * c.n for c in syss) / n_tot, count)
+        tuned = autotune.tune(b, dts, key=key, cache=tune_cache or autotune.DEFAULT_CACHE,
+                              fp32=(precision == 1))
+        tuned = dict(key=key, tuning=tuned["tuning"])
     b.step_async(warmup, dts, stream)
     # per-kernel times: a host-driven pass with CUDA events around each launch
     b.set_timing(True)
@@ -77,7 +87,7 @@ def batched(count=256, steps=2000, warmup=20, precision=1, seed=1004) -> dict:
                 all_pairs_systems=small, list_builds=rebuilds,
                 kernel_ms_per_step=tm["step_ms"] / max(tm["step_launches"], 1),
                 list_build_ms_per_launch=tm["list_ms"] / max(tm["list_launches"], 1),
-                launches_per_step=launches / steps,
+                launches_per_step=launches / steps, autotuned=tuned,
                 precision="fp32-force" if precision == 1 else "fp64")
 
 
