@@ -37,6 +37,7 @@ def main(argv=None):
     p.add_argument("--fp64-queue", type=int, default=None)
     p.add_argument("--autotune", action="store_true")
     p.add_argument("--half", action="store_true", help="half pair list with Newton's third law")
+    p.add_argument("--observables", action="store_true", help="PE, W, KE, T, P after the steps")
     a = p.parse_args(argv)
     import lj_inputs as li
     from paper_1210_3450_gb300 import build
@@ -67,6 +68,8 @@ def main(argv=None):
         s.step(a.steps, a.dt)
         t = s.get_timing()
         listed, inside = s.pair_stats()
+        if a.observables:
+            t["observables"] = s.observables()
     t.update(n=n, listed_per_particle=listed / n, within_rc_per_particle=inside / n)
     if tuned:
         t["autotune"] = tuned
