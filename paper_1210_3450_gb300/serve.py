@@ -63,6 +63,10 @@ class Request:
     skin: float = 0.3
     dt: float = 0.005
     cancel_after: float = math.nan  # seconds after arrival at which the client cancels
+    # initial state: "fcc" fills the box with an FCC lattice; "droplet" puts an FCC
+    # block at density 0.85 in the (more dilute) box, straddling a corner, so its
+    # particles have more partners than the box's mean density predicts
+    layout: str = "fcc"
     # filled in by the server
     admitted: float = math.nan
     finished: float = math.nan
@@ -76,9 +80,18 @@ class Request:
         return (self.n / self.rho) ** (1.0 / 3.0)
 
 
+DROPLET_DENSITY = 0.85
+
+
 def initial_state(r: Request):
     import lj_inputs as li
-    x = li.fcc_positions(r.n, r.box)
+    if r.layout == "droplet":
+        side = (r.n / DROPLET_DENSITY) ** (1.0 / 3.0)
+        x = np.mod(li.fcc_positions(r.n, side) + (r.box - 0.5 * side), r.box)
+    elif r.layout == "fcc":
+        x = li.fcc_positions(r.n, r.box)
+    else:
+        raise ValueError(f"unknown layout {r.layout!r}")
     v = li.maxwell_boltzmann(r.n, r.temperature, r.seed)
     return x, v
 
