@@ -272,13 +272,15 @@ MD_API int md_probe_fma_rate(int kind, int64_t iters, double* fma_per_s);
  *   MD_TUNE_STEP_BLOCK   threads per block of the force + integration kernel: 64, 128, 256
  *   MD_TUNE_STEP_GROUPS  FP32-force partners loaded per iteration, in groups of 4: 1, 2
  *   MD_TUNE_LIST_BLOCK   threads per block of the pair-list build: 64, 128, 256
- *   MD_TUNE_LIST_VARIANT pair-list build variant (0..4; the lists are identical):
+ *   MD_TUNE_LIST_VARIANT pair-list build variant (0..5; the lists are identical):
  *                        0..3 one thread per particle, bit 0 pre-testing candidates
  *                        on the fixed-point shadow positions instead of positions
  *                        rounded to float, bit 1 skipping neighbour rows farther
  *                        than rl in y or z and narrowing the others' x windows;
  *                        4 warp-cooperative (candidates shared by the lanes of a
- *                        row, staged in shared memory)
+ *                        row, staged in shared memory); 5 as 0, each row's
+ *                        candidates for the whole warp first copied into shared
+ *                        memory with coalesced loads
  *   MD_TUNE_STEP_HINT    1: L1 eviction hints on the FP32 step kernel's loads (list
  *                        words not kept in L1, partner positions kept)
  *   MD_TUNE_GRAPH        1: md_step runs its steps in CUDA-graph launches (a loop node of
@@ -293,7 +295,7 @@ MD_API int md_probe_fma_rate(int kind, int64_t iters, double* fma_per_s);
  *                        from a per-thread queue in list order, so that warps run
  *                        it with full lanes; 0: one plain loop over the list.
  *                        Results are identical bit for bit.
- * Defaults 128 / 2 / 128 / 0 / 1 / 1 / 1. The autotuner (paper_1210_3450_gb300.autotune) times the
+ * Defaults 128 / 2 / 128 / 5 / 1 / 1 / 1. The autotuner (paper_1210_3450_gb300.autotune) times the
  * choices on the caller's own systems and sets the fastest. */
 #define MD_TUNE_STEP_BLOCK 0
 #define MD_TUNE_STEP_GROUPS 1

@@ -24,7 +24,7 @@ STEP_BLOCKS = (64, 128, 256)
 STEP_GROUPS = (1, 2)
 STEP_HINTS = (0, 1)
 LIST_BLOCKS = (64, 128, 256)
-LIST_VARIANTS = (0, 1, 2, 3, 4)
+LIST_VARIANTS = (0, 1, 2, 3, 4, 5)
 FP64_QUEUE = (0, 1)
 
 

@@ -172,7 +172,8 @@ struct Tuning {
   int step_block = 128;
   int step_groups = 2;
   int list_block = 128;
-  int list_variant = 0;  // 0..3 per thread (bit 0: fixed-point pre-test; bit 1: row pruning); 4 per warp
+  int list_variant = 5;  // 0..3 per thread (bit 0: fixed-point pre-test; bit 1: row pruning); 4 per warp;
+                         // 5 as 0 with each row's candidates staged in shared memory
   int step_hint = 1;     // 1: L1 eviction hints on the FP32 step kernel's loads
   int fp64_queue = 1;    // 1: FP64 force loop classifies pairs first and queues the maybe-inside ones
 };

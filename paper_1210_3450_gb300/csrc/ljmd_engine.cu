@@ -112,7 +112,7 @@ int Engine::set_tuning(int key, int value) {
       ++struct_ver_;
       return kOK;
     case 3:
-      if (value < 0 || value > 4) break;
+      if (value < 0 || value > 5) break;
       tuning_.list_variant = value;
       ++struct_ver_;
       return kOK;

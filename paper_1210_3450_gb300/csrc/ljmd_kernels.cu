@@ -475,6 +475,21 @@ struct PreTest<1> {
   __device__ __forceinline__ int4 load(int j) const { return p[j]; }
 };
 
+// PRE 0 reading a row's candidates staged in shared memory: slot j sits at
+// s[j - base].
+struct PreTestS {
+  const float4* s;
+  int base;
+  float cx, cy, cz;
+  float lo2, hi2;
+  __device__ __forceinline__ float key(int j) const { return s[j - base].x; }
+  __device__ __forceinline__ float r2(const float4& q) const {
+    const float dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  }
+  __device__ __forceinline__ float4 load(int j) const { return s[j - base]; }
+};
+
 __device__ __forceinline__ float key_of(const float4& q) { return q.x; }
 __device__ __forceinline__ float key_of(const int4& q) { return __int_as_float(q.w); }
 
@@ -488,8 +503,8 @@ __device__ __forceinline__ float key_of(const int4& q) { return __int_as_float(q
 // range end, the particle itself and (half list) the lower slots are masked once
 // per window, the rare shell candidates take the exact test, and the accepted
 // ones are appended in order.
-template <int PRE>
-__device__ __forceinline__ void sweep_range(const PreTest<PRE>& T, ListCtx& o, int lo, int hi, unsigned code,
+template <class T_>
+__device__ __forceinline__ void sweep_range(const T_& T, ListCtx& o, int lo, int hi, unsigned code,
                                             float xlo, float xhi) {
   int b = hi;
   while (lo < b) {
@@ -651,7 +666,7 @@ __device__ __forceinline__ void lane_rows(const DevArrays& a, int cur, const Sys
       const double xs_ = (code & 3u) == 1u ? xi.x - L : ((code & 3u) == 2u ? xi.x + L : xi.x);
       const float xw = (float)xs_;
       if constexpr (PRE == 0) T.cx = xw;
-      sweep_range<PRE>(T, o, lo, hi, code, xw - w, xw + w);
+      sweep_range(T, o, lo, hi, code, xw - w, xw + w);
     }
   }
 }
@@ -870,6 +885,116 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_warp(DevArra
   float4* buf = sbuf + (threadIdx.x & ~31);
   int sys, tl;
   while (next_rebuild_tile(a, sys, tl)) build_tile_warp(a, cur, sys, tl, buf);
+}
+
+// List build with rows staged in shared memory: the same lists, in the same
+// order, as k_build_list (the same per-thread sweep, pre-test and exact test).
+// For each neighbour row (and piece of a row that wraps in x) the warp first
+// copies the union of its lanes' candidate ranges into shared memory with
+// coalesced loads (up to kStage candidates; a wider union, as where a tile's
+// lanes sit on both sides of a box face, is swept from global memory). Each lane
+// then bisects for its window and sweeps it from there: the candidate loads of
+// the sweep, which in k_build_list wait on L1 and often L2 latency, become
+// shared-memory loads. Rows and pieces are visited by the whole warp (a lane
+// without a second piece has an empty range).
+namespace {
+
+constexpr int kStage = 160;  // staged candidates per warp and row piece
+
+__device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, int sys, int tl, float4* buf) {
+  const int lane = threadIdx.x & 31;
+  const SysParams* __restrict__ Pp = a.params + sys;
+  if (!Pp->active) return;  // uniform over the warp
+  const int li = tl * kTile + lane;
+  const int n = Pp->n;
+  const bool act = li < n;
+  const int64_t p_off = Pp->p_off;
+  const int kmax = Pp->kmax;
+  ListCtx o{Pp, a.xref + p_off, a.nbr + list_word(Pp->l_off, tl, kmax, lane, 0), li, 0, kmax, Pp->half != 0,
+            a.checks + sys};
+  if (act) copy_back_slot(a, cur, p_off + li);
+  const int nc = Pp->nc;
+  if (nc == 1) {  // uniform over the warp
+    if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+    list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+    return;
+  }
+  const float4* __restrict__ xf = a.xf + p_off;
+  const int32_t* __restrict__ cst = a.cstart + Pp->c_off;
+  const double L = Pp->L;
+  const float w = Pp->rlf + Pp->wmargin;  // half-width of the x window
+  PreTest<0> T;
+  T.p = xf;
+  T.lo2 = Pp->rl2f_lo;
+  T.hi2 = Pp->rl2f_hi;
+  PreTestS S;
+  S.s = buf;
+  S.lo2 = T.lo2;
+  S.hi2 = T.hi2;
+  int cx = 1, cy = 0, cz = 0;
+  if (act) {
+    const int ci = a.celltmp[p_off + li];
+    cx = ci % nc; cy = (ci / nc) % nc; cz = ci / (nc * nc);
+  }
+#pragma unroll 1
+  for (int rowi = 0; rowi < 9; ++rowi) {
+    const int oz = rowi / 3 - 1, oy = rowi % 3 - 1;
+    int nz = cz + oz, ny = cy + oy;
+    unsigned shz = 0, shy = 0;
+    if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
+    if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
+    const int row = nc * (ny + nc * nz);
+    const double4_32a xi = o.xs[li];  // padding lanes read their zeroed slot
+    // image code 1 adds +L to x_j - x_i, code 2 adds -L: shift the particle instead
+    T.cy = (float)(shy == 1 ? xi.y - L : (shy == 2 ? xi.y + L : xi.y));
+    T.cz = (float)(shz == 1 ? xi.z - L : (shz == 2 ? xi.z + L : xi.z));
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      int lo = 0, hi = 0;
+      unsigned code = (shy << 2) | (shz << 4);
+      if (act) {
+        if (cx == 0) {
+          if (part == 0) { lo = cst[row + nc - 1]; hi = cst[row + nc]; code |= 2u; }  // x image -L
+          else { lo = cst[row]; hi = cst[row + 2]; }
+        } else if (cx == nc - 1) {
+          if (part == 0) { lo = cst[row + nc - 2]; hi = cst[row + nc]; }
+          else { lo = cst[row]; hi = cst[row + 1]; code |= 1u; }                    // x image +L
+        } else if (part == 0) {
+          lo = cst[row + cx - 1]; hi = cst[row + cx + 2];
+        }
+      }
+      const bool ne = lo < hi;
+      if (!__any_sync(kFull, ne)) continue;  // uniform
+      const float xw = (float)((code & 3u) == 1u ? xi.x - L : ((code & 3u) == 2u ? xi.x + L : xi.x));
+      const int u0 = __reduce_min_sync(kFull, ne ? lo : 0x7fffffff);
+      const int u1 = __reduce_max_sync(kFull, ne ? hi : -1);
+      if (u1 - u0 <= kStage) {
+        // stage [u0, u1) and the 3 slots after it (a group of four may read past
+        // its range end; the slot arrays have four spare entries)
+        for (int k = lane; k < u1 - u0 + 3; k += 32) buf[k] = xf[u0 + k];
+        __syncwarp();
+        S.base = u0;
+        S.cx = xw;
+        S.cy = T.cy;
+        S.cz = T.cz;
+        sweep_range(S, o, lo, hi, code, xw - w, xw + w);
+        __syncwarp();  // before the next piece overwrites the buffer
+      } else {
+        T.cx = xw;
+        sweep_range(T, o, lo, hi, code, xw - w, xw + w);
+      }
+    }
+  }
+  list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+}
+
+}  // namespace
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list_staged(DevArrays a, int cur) {
+  __shared__ float4 sbuf[BLOCK / 32][kStage + 4];
+  int sys, tl;
+  while (next_rebuild_tile(a, sys, tl)) build_tile_staged(a, cur, sys, tl, sbuf[threadIdx.x >> 5]);
 }
 
 // ------------------------------------- fused force + velocity-Verlet step
@@ -1762,6 +1887,13 @@ static void launch_build_list_v(const DevArrays& a, int cur, int block, cudaStre
 
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s) {
   switch (tu.list_variant) {
+    case 5:
+      switch (tu.list_block) {
+        case 64: k_build_list_staged<64><<<reb_blocks(a, 64, 16), 64, 0, s>>>(a, cur); break;
+        case 256: k_build_list_staged<256><<<reb_blocks(a, 256, 4), 256, 0, s>>>(a, cur); break;
+        default: k_build_list_staged<128><<<reb_blocks(a, 128, 8), 128, 0, s>>>(a, cur); break;
+      }
+      break;
     case 4:
       switch (tu.list_block) {
         case 64: k_build_list_warp<64><<<reb_blocks(a, 64, 16), 64, 0, s>>>(a, cur); break;

@@ -34,7 +34,7 @@ def main(which: str, out: str) -> None:
     v = li.maxwell_boltzmann(4001, 0.9, 602)
     for prec in (ljmd.MD_FP32_FORCE, ljmd.MD_FP64):
         for graph in (0, 1):
-            for variant in (0, 3, 4):
+            for variant in (0, 3, 4, 5):
                 with ljmd.LJSystem(box, 4001, 2.5, 0.3, prec) as s:
                     s.set_tuning(graph=graph, list_variant=variant)
                     s.set_state(x, v)

@@ -13,7 +13,7 @@ def test_tuning_does_not_change_results(ljmd, precision):
     x, box = li.perturbed_fcc(3000, 0.8442, 0.08, 501)
     v = li.maxwell_boltzmann(3000, 0.9, 502)
     outs = []
-    for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=0, step_hint=0),
+    for tun in [dict(step_block=128, step_groups=1, list_block=128, list_variant=5, step_hint=0),
                 dict(step_block=64, step_groups=2, list_block=256, list_variant=3, step_hint=1),
                 dict(step_block=256, step_groups=2, list_block=64, list_variant=4, step_hint=1),
                 dict(step_block=128, step_groups=1, list_block=128, list_variant=2, step_hint=1),

@@ -89,8 +89,8 @@ def shell_pairs(count=2000, box=300.0, rl=2.8, seed=11):
 _S = shell_pairs()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4],
-                         ids=["float", "fixed", "float-pruned", "fixed-pruned", "warp"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5],
+                         ids=["float", "fixed", "float-pruned", "fixed-pruned", "warp", "staged"])
 def test_list_bit_exact_in_the_shell(ljmd, oracle, variant):
     x, box = _S
     with make(ljmd, x, np.zeros_like(x), box) as s:
@@ -104,7 +104,7 @@ def test_list_bit_exact_in_the_shell(ljmd, oracle, variant):
         np.testing.assert_array_equal(sorted_csr(start, partners), opartners)
 
 
-@pytest.mark.parametrize("variant", [0, 4], ids=["lane", "warp"])
+@pytest.mark.parametrize("variant", [0, 4, 5], ids=["lane", "warp", "staged"])
 @pytest.mark.parametrize("name,x,box", LIST_CONFIGS, ids=LIST_IDS)
 def test_wrap_cells_and_list_bit_exact(ljmd, oracle, name, x, box, variant):
     v = np.zeros_like(x)
