@@ -86,13 +86,17 @@ def shell_pairs(count=2000, box=300.0, rl=2.8, seed=11):
     return np.concatenate([c, c + rl * (1.0 + t) * u]), box
 
 
-_S = shell_pairs()
+# L = 300, and L = 430, the box of the largest system the library takes
+# (N = 2^26 - 1 at rho 0.8442), where the float pre-test's shell is widest
+# (+-9.6e-5 of rl against +-6.7e-5 at L = 300; the pairs span +-4e-4)
+_S = {300: shell_pairs(), 430: shell_pairs(box=430.0, seed=12)}
 
 
+@pytest.mark.parametrize("box_side", [300, 430])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5],
                          ids=["float", "fixed", "float-pruned", "fixed-pruned", "warp", "staged"])
-def test_list_bit_exact_in_the_shell(ljmd, oracle, variant):
-    x, box = _S
+def test_list_bit_exact_in_the_shell(ljmd, oracle, variant, box_side):
+    x, box = _S[box_side]
     with make(ljmd, x, np.zeros_like(x), box) as s:
         s.set_tuning(list_variant=variant)
         s.build_list()
@@ -317,6 +321,25 @@ def test_full_size_sampled_forces(ljmd, oracle):
         rms = np.sqrt((f ** 2).sum(1).mean())
         assert np.abs(f.sum(0)).max() <= (1e-12 if precision == 0 else 1e-4) * len(x) * rms
         assert 70 * len(x) < n_list < 90 * len(x)
+
+
+def _pair_keys(start, partners):
+    """The pairs of a CSR list as sorted (particle << 32 | partner) keys."""
+    seg = np.repeat(np.arange(len(start) - 1, dtype=np.int64), np.diff(start))
+    return np.sort((seg << 32) | partners.astype(np.int64))
+
+
+def test_full_size_list_membership(ljmd, oracle):
+    """The benchmark's size, N = 2,048,000 (FCC 80^3 x 4 at rho 0.8442 displaced by up
+    to 0.1): every particle's list, built by the default variant, equals the oracle's
+    list {j != i : r^2 < rl^2} bit for bit (as sets of caller ids)."""
+    x, box = li.perturbed_fcc(2_048_000, 0.8442, 0.1, 116)
+    with make(ljmd, x, np.zeros_like(x), box) as s:
+        s.build_list()
+        start, partners = s.get_list()
+    ostart, opartners = oracle.build_list(oracle.wrap(x, box), box, 2.8)
+    np.testing.assert_array_equal(start, ostart)
+    assert np.array_equal(_pair_keys(start, partners), _pair_keys(ostart, opartners))
 
 
 def test_cavitation_size_sampled_forces(ljmd, oracle):
