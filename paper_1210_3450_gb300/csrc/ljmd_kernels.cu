@@ -1224,7 +1224,58 @@ __device__ __forceinline__ double force_factor(double r2, double c2x8) {
 // queue keeps list order and the pairs left out are outside rc, where the force
 // is zero, so every force is summed in the same order as a plain loop over the
 // list: the results are the same bit for bit.
-constexpr int kQueue64 = 16;  // queued list words per thread (FP64 force loop)
+constexpr int kQueue64 = 16;  // queued list words per thread (FP64 pair loops)
+
+// The classify-and-queue loop of the FP64 pair loops: every thread of the warp
+// calls it (cnt = 0 for a lane without a particle); body(e) runs for the list
+// words e of the thread's maybe-inside pairs, in list order, in rounds where
+// every thread with a queued pair takes one. qme points at the thread's queue
+// column (entry q at qme[q * BLOCK]).
+template <int BLOCK, class Body>
+__device__ __forceinline__ void queued_pairs(const DevArrays& a, const TileCtx& t, const SysParams& P, int lane,
+                                             int cur, int cnt, uint32_t* qme, Body&& body) {
+  const uint4* lp4 = (const uint4*)(a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0));
+  const int4* qs = a.xq[cur] + P.p_off;
+  const int4 qi = t.act ? qs[t.local] : make_int4(0, 0, 0, 0);
+  const float rc2q = P.rc2q_hi;
+  const uint32_t self = (uint32_t)t.local;
+  int k = 0;  // next listed partner to classify
+  unsigned head = 0u, tail = 0u;
+  while (true) {
+    const unsigned qn = tail - head;
+    const bool left = k < cnt;
+    const unsigned has = __ballot_sync(kFull, qn > 0u);
+    const unsigned busy = __ballot_sync(kFull, qn > 0u || left);
+    if (busy == 0u) break;
+    const unsigned room = __ballot_sync(kFull, left && qn <= (unsigned)(kQueue64 - 4));
+    if (has == busy || room == 0u) {
+      // FP64 round: each thread with a queued pair takes the next one
+      if (qn > 0u) {
+        const uint32_t e = qme[(head & (kQueue64 - 1)) * BLOCK];
+        ++head;
+        body(e);
+      }
+    } else if ((room >> (threadIdx.x & 31)) & 1u) {  // the ballot's bit of this thread
+      // classification of the next four listed partners (no FP64 instruction)
+      const uint4 w = __ldg(lp4 + (int64_t)(k >> 2) * kTile);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const bool ok = k + m < cnt;
+        const int4 qj = qs[ok ? partner_slot(a, t.sys, ws[m], P.n, self) : self];
+        const float ax = (float)wrapped_diff(qj.x, qi.x);
+        const float ay = (float)wrapped_diff(qj.y, qi.y);
+        const float az = (float)wrapped_diff(qj.z, qi.z);
+        if (ok && fmaf(az, az, fmaf(ay, ay, ax * ax)) < rc2q) {
+          qme[(tail & (kQueue64 - 1)) * BLOCK] = ws[m];
+          ++tail;
+        }
+      }
+      k += 4;
+    }
+  }
+}
+
 
 // QUEUE false: the plain loop over the list (every listed pair takes the FP64
 // separation and r^2, the warp pays the force body whenever one lane is inside).
@@ -1275,64 +1326,27 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp64(DevArrays a, int cur, doubl
     }
   } else {  // every lane of the warp takes part (inactive ones with an empty list)
     const int cnt = t.act ? list_count(a, t.sys, t.s, P.kmax) : 0;
-    const uint4* lp4 = (const uint4*)(a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0));
-    const int4* qs = a.xq[cur] + P.p_off;
     const double4_32a* xs = a.x[cur] + P.p_off;
-    const int4 qi = t.act ? qs[t.local] : make_int4(0, 0, 0, 0);
     const long long rc2b = __double_as_longlong(P.rc2);
-    const float rc2q = P.rc2q_hi;
     const double c2x8 = 8.0 * P.c2, L = P.L;
     const uint32_t self = (uint32_t)t.local;
-    uint32_t* qme = &qbuf[0][threadIdx.x];
-    int k = 0;                 // next listed partner to classify
-    unsigned head = 0u, tail = 0u;
-    while (true) {
-      const unsigned qn = tail - head;
-      const bool left = k < cnt;
-      const unsigned has = __ballot_sync(kFull, qn > 0u);
-      const unsigned busy = __ballot_sync(kFull, qn > 0u || left);
-      if (busy == 0u) break;
-      const unsigned room = __ballot_sync(kFull, left && qn <= (unsigned)(kQueue64 - 4));
-      if (has == busy || room == 0u) {
-        // FP64 round: each thread with a queued pair takes the next one
-        if (qn > 0u) {
-          const uint32_t e = qme[(head & (kQueue64 - 1)) * BLOCK];
-          ++head;
-          const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, self)];
-          double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-          const unsigned code = e >> kIdxBits;
-          if (code) {
-            dx = apply_image(dx, code & 3u, L);
-            dy = apply_image(dy, (code >> 2) & 3u, L);
-            dz = apply_image(dz, (code >> 4) & 3u, L);
-          }
-          const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-          if (__double_as_longlong(r2) < rc2b) {
-            const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
-            Fx = fma(g, dx, Fx);
-            Fy = fma(g, dy, Fy);
-            Fz = fma(g, dz, Fz);
-          }
-        }
-      } else if ((room >> lane) & 1u) {
-        // classification of the next four listed partners (no FP64 instruction)
-        const uint4 w = __ldg(lp4 + (int64_t)(k >> 2) * kTile);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const bool ok = k + m < cnt;
-          const int4 qj = qs[ok ? partner_slot(a, t.sys, ws[m], P.n, self) : self];
-          const float ax = (float)wrapped_diff(qj.x, qi.x);
-          const float ay = (float)wrapped_diff(qj.y, qi.y);
-          const float az = (float)wrapped_diff(qj.z, qi.z);
-          if (ok && fmaf(az, az, fmaf(ay, ay, ax * ax)) < rc2q) {
-            qme[(tail & (kQueue64 - 1)) * BLOCK] = ws[m];
-            ++tail;
-          }
-        }
-        k += 4;
+    queued_pairs<BLOCK>(a, t, P, lane, cur, cnt, &qbuf[0][threadIdx.x], [&](uint32_t e) {
+      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, self)];
+      double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+      const unsigned code = e >> kIdxBits;
+      if (code) {
+        dx = apply_image(dx, code & 3u, L);
+        dy = apply_image(dy, (code >> 2) & 3u, L);
+        dz = apply_image(dz, (code >> 4) & 3u, L);
       }
-    }
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      if (__double_as_longlong(r2) < rc2b) {
+        const double g = force_factor<MODE>(r2, c2x8);  // 24 r^-8 - 48 r^-14 + 8 c2
+        Fx = fma(g, dx, Fx);
+        Fy = fma(g, dy, Fy);
+        Fz = fma(g, dz, Fz);
+      }
+    });
   }
   unsigned long long d2b = 0ull;
   if (t.act) d2b = integrate<false>(a, P, t, cur, xi, Fx, Fy, Fz, ka, kb, flags);
@@ -1464,30 +1478,33 @@ __global__ void __launch_bounds__(kBlock) k_integrate_half(DevArrays a, int cur,
 // 1/2), and 1/2 |v|^2; each tile sums its 32 values in a fixed shuffle order into
 // tile_obs[3 t ...]. With V(r) = 4 (r^-12 - r^-6) + 4 c2 r^2 + 4 c0 (Eq. 1) and
 // -r V'(r) = 48 r^-12 - 24 r^-6 - 8 c2 r^2, the pair loop only sums r^-12, r^-6
-// and r^2 and counts the pairs inside rc: 9 FP64 operations per pair inside rc
-// and 6 per listed pair (the periodic image is added only where the list word
-// names one; the cutoff and range tests compare bit patterns, r^2 >= 0).
+// and r^2 and counts the pairs inside rc. Like the FP64 force loop it classifies
+// the listed pairs on the fixed-point shadows first and runs the FP64 arithmetic
+// (6 operations for the separation and r^2, 9 for a pair inside rc; the periodic
+// image added only where the list word names one, the cutoff tested on bit
+// patterns, r^2 >= 0) in full-warp rounds from per-thread queues; the sums keep
+// list order, so the results equal a plain loop's bit for bit.
 __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int with_pairs,
                                                       const int32_t* __restrict__ select) {
+  __shared__ uint32_t qbuf[kQueue64][kBlock];
   TileCtx t;
   SysParams P;
-  if (!tile_ctx(a, t, P)) return;
-  if (select && !select[t.sys]) return;
+  if (!tile_ctx(a, t, P)) return;           // uniform over the warp
+  if (select && !select[t.sys]) return;     // uniform over the warp
   const int lane = threadIdx.x & 31;
   double pe = 0.0, w = 0.0, ke = 0.0;
-  if (t.act && with_pairs) {
-    const double4_32a xi = a.x[cur][t.s];
+  if (with_pairs) {  // every lane takes part (inactive ones with an empty list)
+    const double4_32a xi = t.act ? a.x[cur][t.s] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
     const double4_32a* xs = a.x[cur] + P.p_off;
-    const int cnt = list_count(a, t.sys, t.s, P.kmax);
-    const uint32_t* lp = a.nbr + list_word(P.l_off, t.tl, P.kmax, lane, 0);
+    const int cnt = t.act ? list_count(a, t.sys, t.s, P.kmax) : 0;
     const long long rc2b = __double_as_longlong(P.rc2);
     const long long tinyb = __double_as_longlong(1e-30);
     const double L = P.L;
+    const uint32_t self = (uint32_t)t.local;
     double s12 = 0.0, s6 = 0.0, sr = 0.0;
     int nin = 0;
-    for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = __ldg(lp + (int64_t)(k >> 2) * (4 * kTile) + (k & 3));
-      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, (uint32_t)t.local)];
+    queued_pairs<kBlock>(a, t, P, lane, cur, cnt, &qbuf[0][threadIdx.x], [&](uint32_t e) {
+      const double4_32a xj = xs[partner_slot(a, t.sys, e, P.n, self)];
       double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
       const unsigned code = e >> kIdxBits;
       if (code) {
@@ -1507,13 +1524,15 @@ __global__ void __launch_bounds__(kBlock) k_pe_virial(DevArrays a, int cur, int 
         sr += r2;
         ++nin;
       }
-    }
-    const double c2 = P.c2;
-    pe = 4.0 * (s12 - s6) + 4.0 * fma(c2, sr, P.c0 * (double)nin);
-    w = 48.0 * s12 - 24.0 * s6 - 8.0 * c2 * sr;
-    if (!P.half) {  // the full list counts each pair twice
-      pe *= 0.5;
-      w *= 0.5;
+    });
+    if (t.act) {
+      const double c2 = P.c2;
+      pe = 4.0 * (s12 - s6) + 4.0 * fma(c2, sr, P.c0 * (double)nin);
+      w = 48.0 * s12 - 24.0 * s6 - 8.0 * c2 * sr;
+      if (!P.half) {  // the full list counts each pair twice
+        pe *= 0.5;
+        w *= 0.5;
+      }
     }
   }
   if (t.act) {
