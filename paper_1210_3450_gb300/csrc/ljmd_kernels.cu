@@ -152,22 +152,36 @@ __global__ void k_to_caller(DevArrays a, int cur, int which, double* __restrict_
 
 // --------------------------------------------------------- binning (Sec. 2.1)
 
+// Count with one atomic per distinct cell of the warp: between builds a tile's
+// particles (in the previous build's cell order) mostly stay in one or two cells.
+// Every lane of the warp calls this (c < 0: no particle).
+__device__ __forceinline__ int warp_cell_add(int32_t* counts, int c) {
+  const unsigned same = __match_any_sync(kFull, c);
+  const int leader = __ffs(same) - 1;
+  int base = 0;
+  if (c >= 0 && (threadIdx.x & 31) == leader) base = atomicAdd(&counts[c], __popc(same));
+  base = __shfl_sync(kFull, base, leader);
+  return base + __popc(same & ((1u << (threadIdx.x & 31)) - 1u));  // this lane's place in the group
+}
+
 __global__ void k_cell_count(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
-    if (!t.act) return;
     // Positions are wrapped into [0, L) only here (at a list build): between
     // builds they move freely so that the periodic images stored in the list
     // stay valid.
-    const double4_32a x = a.x[cur][t.s];
-    const double4_32a w = make_double4_32a(wrap_fast(x.x, P.L), wrap_fast(x.y, P.L), wrap_fast(x.z, P.L), 0.0);
-    if (w.x != x.x || w.y != x.y || w.z != x.z) a.x[cur][t.s] = w;
-    int c = 0;
-    if (P.nc > 1) {
-      c = cell_of(w, P.inv_cs, P.nc);
-      if (!check_ok(a, t.sys, c >= 0 && c < P.nc * P.nc * P.nc, kChkCell)) c = 0;
-      atomicAdd(&a.ccount[P.c_off + c], 1);
+    int c = -1;
+    if (t.act) {
+      const double4_32a x = a.x[cur][t.s];
+      const double4_32a w = make_double4_32a(wrap_fast(x.x, P.L), wrap_fast(x.y, P.L), wrap_fast(x.z, P.L), 0.0);
+      if (w.x != x.x || w.y != x.y || w.z != x.z) a.x[cur][t.s] = w;
+      c = 0;
+      if (P.nc > 1) {
+        c = cell_of(w, P.inv_cs, P.nc);
+        if (!check_ok(a, t.sys, c >= 0 && c < P.nc * P.nc * P.nc, kChkCell)) c = 0;
+      }
+      a.cell[t.s] = c;
     }
-    a.cell[t.s] = c;
+    if (P.nc > 1) warp_cell_add(a.ccount + P.c_off, c);  // uniform over the warp
   });
 }
 
@@ -286,13 +300,14 @@ __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nre
 
 __global__ void k_scatter(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
-    if (!t.act) return;
-    if (P.nc == 1) {
-      a.perm[t.s] = t.local;
+    if (P.nc == 1) {  // uniform over the warp
+      if (t.act) a.perm[t.s] = t.local;
       return;
     }
-    const int c = a.cell[t.s];
-    const int pos = a.cstart[P.c_off + c] + atomicAdd(&a.ccount[P.c_off + c], 1);
+    const int c = t.act ? a.cell[t.s] : -1;
+    const int k = warp_cell_add(a.ccount + P.c_off, c);  // fill counter, one atomic per cell of the warp
+    if (!t.act) return;
+    const int pos = a.cstart[P.c_off + c] + k;
     if (!check_ok(a, t.sys, pos < a.cstart[P.c_off + c + 1], kChkScatter)) return;
     const int64_t d = P.p_off + pos;
     a.perm[d] = t.local;
