@@ -273,6 +273,31 @@ def test_list_overflow_grows_capacity(ljmd, oracle):
     np.testing.assert_array_equal(sorted_csr(start, partners), opartners)
 
 
+def _raw_list(ljmd, x, box, variant, half=False):
+    with ljmd.LJSystem(box, len(x), 2.5, 0.3) as s:
+        s.set_pair_list(ljmd.MD_LIST_HALF if half else ljmd.MD_LIST_FULL)
+        s.set_tuning(list_variant=variant)
+        s.set_state(x, np.zeros_like(x))
+        s.build_list()
+        return s.get_list()
+
+
+@pytest.mark.parametrize("half", [False, True], ids=["full", "half"])
+def test_list_order_equal_across_variants(ljmd, half):
+    """Every build variant writes the same partners in the same order (the
+    force sums, and so the trajectories, depend on the order), on the wrap and
+    cell-face configurations and on corner-packed particles that overflow the
+    initial capacity (the list is built again after it grows)."""
+    cases = [(n, x, box) for n, x, box in LIST_CONFIGS]
+    cases.append(("corner-packed", li.uniform_positions(1500, 6.0, 110), 20.0))
+    for name, x, box in cases:
+        ref = _raw_list(ljmd, x, box, 0, half)
+        for variant in (1, 2, 3, 5) if half else (1, 2, 3, 4, 5):
+            got = _raw_list(ljmd, x, box, variant, half)
+            np.testing.assert_array_equal(got[0], ref[0], err_msg=f"{name} variant {variant}")
+            np.testing.assert_array_equal(got[1], ref[1], err_msg=f"{name} variant {variant}")
+
+
 def test_single_particle_and_dimer(ljmd, oracle):
     with make(ljmd, np.array([[1.0, 2.0, 3.0]]), np.zeros((1, 3)), 10.0) as s:
         assert np.all(s.forces() == 0.0)
