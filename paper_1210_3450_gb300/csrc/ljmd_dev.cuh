@@ -130,7 +130,8 @@ struct DevArrays {
   unsigned long long* disp2;  // per system: max squared displacement, or max |v|^2 (double bits)
   double* margin;             // per system: velocity-bound rule's remaining margin
   const int32_t* rebuild;     // per system: 1 if it rebuilds in the current pass
-  const int32_t* rebuild_ids; // ids of the systems that rebuild (compact)
+  const int32_t* rebuild_ids; // ids of the systems that rebuild (compact, costliest tiles first)
+  const int32_t* sys_order;   // system ids by descending list-build cost per tile
   const int32_t* reb_pref;    // exclusive prefix of the rebuilding systems' tile counts (nreb + 1)
   int32_t* chunk_pref;        // exclusive prefix of the rebuilding systems' cell-chunk counts (nreb + 1)
   int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems (scan scratch)

@@ -290,7 +290,7 @@ void Engine::free_all() {
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.skey); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
   dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
-  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_checks_); dfree(d_rebuild_); dfree(d_tile_sys_);
+  dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_checks_); dfree(d_rebuild_); dfree(d_order_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_); hfree(h_obs_work_);
   drop_graphs();
@@ -388,6 +388,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_checks_, ns));
   CK(cudaMemset(d_checks_, 0, sizeof(int32_t) * ns));
   CKR(dmalloc(&d_rebuild_, 4 * ns + 2));
+  CKR(dmalloc(&d_order_, ns));
   CKR(dmalloc(&d_tile_sys_, T));
   CKR(dmalloc(&d_obs_, 3 * ns));
   CKR(dmalloc(&d_obs_work_, 2 * ns + 1));
@@ -580,6 +581,34 @@ int Engine::upload_params(int only) {
     P.half = half_ ? 1 : 0;
   }
   CK(cudaMemcpy(d_params_ + k0, ps.data(), sizeof(SysParams) * ps.size(), cudaMemcpyHostToDevice));
+  return upload_order();
+}
+
+// Order in which rebuild passes take the systems: descending estimated list-build
+// cost per tile, so that the warps fetching tiles start the slowest first and a
+// pass does not end on a few slow tiles. The estimate counts a particle's
+// candidates (9 rows of 3 cells cut to a window of 2 rl, or every particle when
+// nc == 1) and half its expected partners. Results do not depend on the order.
+int Engine::upload_order() {
+  const int ns = nsys();
+  if (ns == 0) return kOK;
+  std::vector<double> cost((size_t)ns, -1.0);
+  for (int k = 0; k < ns; ++k) {
+    const SysHost& h = sys_[k];
+    if (!h.used) continue;
+    const double L = h.spec.L, rho = (double)h.spec.n / (L * L * L);
+    const double partners = 4.0 / 3.0 * M_PI * h.rl * h.rl * h.rl * rho;
+    const double cs = L / h.nc;
+    const double cand = h.nc == 1 ? (double)h.spec.n : 9.0 * cs * cs * 2.0 * h.rl * rho;
+    cost[(size_t)k] = cand + 0.5 * partners;
+  }
+  std::vector<int32_t> order((size_t)ns);
+  for (int k = 0; k < ns; ++k) order[(size_t)k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t p, int32_t q) { return cost[(size_t)p] > cost[(size_t)q]; });
+  order_rank_.assign((size_t)ns, 0);
+  for (int i = 0; i < ns; ++i) order_rank_[(size_t)order[(size_t)i]] = i;
+  CK(cudaMemcpy(d_order_, order.data(), sizeof(int32_t) * (size_t)ns, cudaMemcpyHostToDevice));
   return kOK;
 }
 
@@ -592,6 +621,7 @@ DevArrays Engine::arrays() const {
   a.checks = d_checks_;
   a.rebuild = d_rebuild_;
   a.rebuild_ids = d_rebuild_ + nsys();
+  a.sys_order = d_order_;
   a.reb_pref = d_rebuild_ + 2 * nsys();
   a.chunk_pref = d_rebuild_ + 3 * nsys() + 1;
   a.nreb = 0;
@@ -717,6 +747,8 @@ int Engine::read_checks(cudaStream_t s) {
 // Full rebuild (bin, stable counting sort, gather, list) of the given systems.
 int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
   if (which.empty()) return kOK;
+  std::sort(which.begin(), which.end(),
+            [&](int p, int q) { return order_rank_[(size_t)p] < order_rank_[(size_t)q]; });
   for (int attempt = 0; attempt < 4; ++attempt) {
     for (int k = 0; k < nsys(); ++k) h_rebuild_[k] = 0;
     int32_t* pref = h_rebuild_ + 2 * nsys();

@@ -166,6 +166,7 @@ class Engine {
   int alloc_arrays();
   void free_all();
   int upload_params(int only = -1);
+  int upload_order();
   int upload_tiles(int k, int32_t value);
   int grow_list_arena(int64_t min_extra_units);
   void update_extent();
@@ -239,6 +240,8 @@ class Engine {
   int32_t* d_checks_ = nullptr;  // per system: failed device checks (checked build)
   int32_t* d_rebuild_ = nullptr;  // flags (nsys), compact ids (nsys), tile prefix (nsys + 1), chunk prefix (nsys + 1)
   int32_t* d_tile_sys_ = nullptr;
+  int32_t* d_order_ = nullptr;    // system ids by descending list-build cost per tile
+  std::vector<int32_t> order_rank_;  // position of each system in that order
   double* d_obs_ = nullptr;
   int32_t* d_obs_work_ = nullptr;  // selected systems and their chunk prefix (observables)
   int32_t* h_obs_work_ = nullptr;

@@ -1726,7 +1726,8 @@ void launch_to_caller(const DevArrays& a, int cur, int which, double* out, int64
 // forms test 2 sqrt(d2) >= skin. Velocity-bound rule (the DUTC check): the
 // margin, the whole skin after a rebuild, shrinks by 2 v_max dt each step, and
 // the list is rebuilt when it is no longer positive. Writes the rebuild flags
-// and the rebuilding systems in ascending order, resets the per-step maxima, and
+// and the rebuilding systems (in the order of sys_order: costliest list-build
+// tiles first), resets the per-step maxima, and
 // in a graph (reb_count set) counts steps, passes and rebuilds and sets the
 // conditions of the rebuild node (h_if) and, after the second step of the loop
 // body (last), of the loop node (h_loop). A non-finite position or velocity
@@ -1752,10 +1753,11 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) { base_s = 0; bad_s = 0; }
   __syncthreads();
-  for (int k0 = 0; k0 < nsys; k0 += (int)blockDim.x) {
-    const int k = k0 + (int)threadIdx.x;
+  for (int i0 = 0; i0 < nsys; i0 += (int)blockDim.x) {
+    const int i = i0 + (int)threadIdx.x;
+    const int k = i < nsys ? a.sys_order[i] : -1;
     int need = 0;
-    if (k < nsys) {
+    if (k >= 0) {
       const unsigned long long d2 = a.disp2[k];
       a.disp2[k] = 0ull;
       const SysParams& P = a.params[k];

@@ -279,8 +279,12 @@ class MDServer:
 
     def summary(self, reqs: list[Request], wall: float) -> dict:
         done = [r for r in self.done if "rejected" not in r.result and "cancelled" not in r.result]
-        lat = np.array([r.finished - r.arrival for r in done]) if done else np.array([math.nan])
-        wait = np.array([r.admitted - r.arrival for r in done]) if done else np.array([math.nan])
+        lat = np.array([r.finished - r.arrival for r in done])
+        wait = np.array([r.admitted - r.arrival for r in done])
+
+        def pct(a, q):  # NaN when no request completed
+            return float(np.percentile(a, q)) if a.size else math.nan
+
         done_ids = {id(r) for r in self.done}
         left = [r for r in reqs if id(r) not in done_ids]
         left_work = sum(r.n * (r.remaining if r.sid >= 0 and not math.isnan(r.admitted) else r.steps)
@@ -290,10 +294,10 @@ class MDServer:
                     rejected=sum(1 for r in self.done if "rejected" in r.result),
                     cancelled=sum(1 for r in self.done if "cancelled" in r.result),
                     unfinished=len(left), wall_s=wall,
-                    p50_latency_s=float(np.nanpercentile(lat, 50)),
-                    p99_latency_s=float(np.nanpercentile(lat, 99)),
-                    p50_queue_s=float(np.nanpercentile(wait, 50)),
-                    p99_queue_s=float(np.nanpercentile(wait, 99)),
+                    p50_latency_s=pct(lat, 50),
+                    p99_latency_s=pct(lat, 99),
+                    p50_queue_s=pct(wait, 50),
+                    p99_queue_s=pct(wait, 99),
                     particle_steps_per_s=rate,
                     gpu_busy_fraction=self.gpu_busy / wall if wall > 0 else math.nan,
                     remaining_particle_steps=int(left_work),
