@@ -419,6 +419,8 @@ struct ListCtx {
   int kmax;
   bool half;              // half list: only partners in higher slots
   int32_t* chk;           // the system's check word (checked build)
+  uint32_t* wp = out;     // where entry `count` goes (entries 4 m .. 4 m + 3 are 16
+                          // contiguous bytes; the next four follow 4 kTile words on)
   // The checked build verifies each appended partner: a slot of the system, not
   // the particle itself.
   __device__ __forceinline__ bool entry_ok(uint32_t e) const {
@@ -428,16 +430,39 @@ struct ListCtx {
     atomicOr(chk, kChkListEntry);
     return false;
   }
+  __device__ __forceinline__ void advance() {
+    ++count;
+    wp += (count & 3) ? 1 : 4 * kTile - 3;
+  }
   // Append e when p holds (a predicated store).
   __device__ __forceinline__ void push_if(bool p, uint32_t e) {
-    if (p && !entry_ok(e)) return;
-    if (p && count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
-    count += p ? 1 : 0;
+    if (!p) return;
+    push(e);
   }
   __device__ __forceinline__ void push(uint32_t e) {
     if (!entry_ok(e)) return;
-    if (count < kmax) out[(int64_t)(count >> 2) * (4 * kTile) + (count & 3)] = e;
-    ++count;
+    if (count < kmax) *wp = e;
+    advance();
+  }
+  // Append candidates j0 + k (image bits cbits) for the set bits k of `bits`, in
+  // ascending k; the capacity is checked once for all of them.
+  __device__ __forceinline__ void push_bits(unsigned bits, int j0, uint32_t cbits) {
+    if (count + __popc(bits) <= kmax) {
+      while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const uint32_t e = (uint32_t)(j0 + k) | cbits;
+        if (!entry_ok(e)) continue;
+        *wp = e;
+        advance();
+      }
+    } else {
+      while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        push((uint32_t)(j0 + k) | cbits);
+      }
+    }
   }
   // Whether candidate j with image code (not 0xff) passes the exact FP64 test.
   __device__ __forceinline__ bool exact_in(int j, unsigned code) const {
@@ -570,11 +595,7 @@ __device__ __forceinline__ void sweep_range(const T_& T, ListCtx& o, int lo, int
       shell &= shell - 1u;
       if (o.exact_in(j0 + k, code)) in |= 1u << k;
     }
-    while (in) {
-      const int k = __ffs(in) - 1;
-      in &= in - 1u;
-      o.push((uint32_t)(j0 + k) | cbits);
-    }
+    o.push_bits(in, j0, cbits);
   }
 }
 
