@@ -121,7 +121,7 @@ struct DevArrays {
   int32_t* idtmp;
   int32_t* celltmp;
   int32_t* perm;      // scattered position -> old slot (cell order, arbitrary within a cell)
-  int32_t* perm2;     // new slot -> old slot (within a cell by x, then caller index)
+  int32_t* perm2;     // caller index of each scattered position (the ranking's tie-break)
   int32_t* ccount;    // particles per cell (then fill counters)
   int32_t* cstart;    // first slot of each cell (relative to the system), ncell + 1 per system
   // systems
@@ -134,7 +134,7 @@ struct DevArrays {
   const int32_t* sys_order;   // system ids by descending list-build cost per tile
   const int32_t* reb_pref;    // exclusive prefix of the rebuilding systems' tile counts (nreb + 1)
   int32_t* chunk_pref;        // exclusive prefix of the rebuilding systems' cell-chunk counts (nreb + 1)
-  int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems (scan scratch)
+  int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems (summed by the count)
   int32_t chunk_cap;          // entries of chunk_sum
   int32_t nreb;               // rebuilding systems (host-driven passes; the graph reads ctl->nreb)
   int32_t* tile_next;         // work counter of the list build (reset before each build)
@@ -183,16 +183,19 @@ struct Tuning {
 // All launches cover every tile of every active system; warps of inactive
 // systems (or of systems not rebuilding, for the rebuild kernels) return early.
 
-// Kernels of one rebuild pass: count, the two scan passes, scatter, rank, gather,
-// list build (which also copies the gathered state back into place).
-constexpr int kRebuildLaunches = 7;
+// Kernels of one rebuild pass: count (with the scan's chunk totals), scan, scatter,
+// rank with gather, list build (which also copies the gathered state back into
+// place).
+constexpr int kRebuildLaunches = 5;
 
+// Counts the rebuilding systems' particles per cell and per scan chunk; the chunk
+// totals must be zero before (the decision or the host-driven pass clears them).
 void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s);
-// Exclusive scan of the cell counts into the cell starts (two launches).
+// Exclusive scan of the cell counts into the cell starts.
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s);
 void launch_scatter(const DevArrays& a, int cur, cudaStream_t s);
-void launch_cell_rank(const DevArrays& a, cudaStream_t s);
-void launch_gather(const DevArrays& a, int cur, cudaStream_t s);
+// In-cell order and gather into it.
+void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s);
 void launch_build_list(const DevArrays& a, int cur, const Tuning& tu, cudaStream_t s);
 // Device-side list-validity decision of the graph-captured loop (see GraphCtl).
 // reb_count NULL: outside a graph (no step or pass counting, no node conditions).

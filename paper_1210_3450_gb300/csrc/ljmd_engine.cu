@@ -766,6 +766,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     pref[nreb] = tiles;
     cpref[nreb] = chunks;
     CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (4 * nsys() + 2), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_.chunk_sum, 0, sizeof(int32_t) * (size_t)chunks, s));  // totalled by the count
     CK(cudaMemsetAsync(d_status_, 0, sizeof(SysStatus) * nsys(), s));
     CK(cudaMemsetAsync(&d_ctl_->next_tile, 0, sizeof(int32_t), s));
     DevArrays a = arrays();
@@ -774,8 +775,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     launch_cell_count(a, cur_, s);
     launch_cell_scan(a, nreb, s);
     launch_scatter(a, cur_, s);
-    launch_cell_rank(a, s);
-    launch_gather(a, cur_, s);
+    launch_cell_rank(a, cur_, s);
     tmark_end(s);
     tmark_begin(kTList, s);
     launch_build_list(a, cur_, list_tuning(), s);
@@ -987,8 +987,7 @@ int Engine::build_graph(cudaGraph_t g, int parity) {
       launch_cell_count(a, c1, cap_[1]);
       launch_cell_scan(a, nused, cap_[1]);
       launch_scatter(a, c1, cap_[1]);
-      launch_cell_rank(a, cap_[1]);
-      launch_gather(a, c1, cap_[1]);
+      launch_cell_rank(a, c1, cap_[1]);
       launch_build_list(a, c1, list_tuning(), cap_[1]);
       cudaGraph_t t1 = nullptr;
       e = cudaStreamEndCapture(cap_[1], &t1);

@@ -35,6 +35,7 @@ struct TileCtx {
   int local;    // slot index within the system
   int64_t s;    // global slot
   bool act;     // lane holds a particle
+  int r;        // rebuild passes: the system's place among the rebuilding systems
 };
 
 // Returns false if the whole warp has nothing to do.
@@ -74,6 +75,7 @@ __device__ __forceinline__ bool reb_tile(const DevArrays& a, int nreb, int w, Ti
     else hi = mid - 1;
   }
   t.sys = a.rebuild_ids[lo];
+  t.r = lo;
   P = a.params[t.sys];
   if (!P.active) return false;
   t.tl = w - a.reb_pref[lo];
@@ -181,16 +183,20 @@ __global__ void k_cell_count(DevArrays a, int cur) {
       }
       a.cell[t.s] = c;
     }
-    if (P.nc > 1) warp_cell_add(a.ccount + P.c_off, c);  // uniform over the warp
+    if (P.nc > 1) {  // uniform over the warp
+      warp_cell_add(a.ccount + P.c_off, c);
+      // the scan's chunk totals (zeroed by the pass's decision), one atomic per chunk of the warp
+      warp_cell_add(a.chunk_sum, c >= 0 ? a.chunk_pref[t.r] + c / kScanChunk : -1);
+    }
   });
 }
 
-// Exclusive scan of the cell counts of the rebuilding systems, in two passes over
-// chunks of kScanChunk cells so that a large system spreads over many blocks:
-// k_cell_sums totals each chunk, k_cell_starts adds the totals of the system's
-// earlier chunks to a block scan of its own chunk and writes the starts. Work
-// item w is chunk w - chunk_pref[r] of rebuilding system r. The counts are reset
-// to serve as fill counters of the scatter.
+// Exclusive scan of the cell counts of the rebuilding systems over chunks of
+// kScanChunk cells, so that a large system spreads over many blocks: the count
+// kernel also totals each chunk (chunk_sum), and k_cell_starts adds the totals of
+// the system's earlier chunks to a block scan of its own chunk and writes the
+// starts. Work item w is chunk w - chunk_pref[r] of rebuilding system r. The
+// counts are reset to serve as fill counters of the scatter.
 constexpr int kScanBlock = kScanChunk / 4;
 
 __device__ __forceinline__ int chunk_system(const DevArrays& a, int nreb, int w) {
@@ -213,27 +219,6 @@ __device__ __forceinline__ int block_sum(int v, int* ws) {
   t = __reduce_add_sync(kFull, t);
   __syncthreads();  // ws is reused by the caller's next block-wide step
   return t;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_cell_sums(DevArrays a, int nreb) {
-  if (a.ctl) nreb = a.ctl->nreb;  // graph-captured loop: the count is decided on the device
-  if (nreb <= 0) return;
-  __shared__ int ws[kScanBlock / 32];
-  const int total = a.chunk_pref[nreb];
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const int r = chunk_system(a, nreb, w);
-    const int sys = a.rebuild_ids[r];
-    const SysParams& P = a.params[sys];
-    if (!P.active || !a.rebuild[sys]) continue;  // uniform over the block
-    const int64_t ncell = (int64_t)P.nc * P.nc * P.nc;
-    const int64_t c0 = (int64_t)(w - a.chunk_pref[r]) * kScanChunk + 4 * threadIdx.x;
-    const int32_t* cnt = a.ccount + P.c_off;
-    int part = 0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) part += c0 + m < ncell ? cnt[c0 + m] : 0;
-    part = block_sum(part, ws);
-    if (threadIdx.x == 0) a.chunk_sum[w] = part;
-  }
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nreb) {
@@ -295,8 +280,8 @@ __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nre
 
 // Scatter into cell order (arbitrary within a cell). Beside the old slot, the
 // scattered position receives the particle's sort key (x, then caller index) and
-// cell, so that the ranking below reads them contiguously (the id and cell go to
-// the gather's scratch arrays, unused until the gather).
+// cell, so that the ranking below reads them contiguously (the caller index goes
+// to perm2, the cell to the cell scratch).
 
 __global__ void k_scatter(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
@@ -313,63 +298,56 @@ __global__ void k_scatter(DevArrays a, int cur) {
     a.perm[d] = t.local;
     // x >= 0 (wrapped at the count), so its bit pattern orders like the value
     a.skey[d] = __double_as_longlong(a.x[cur][t.s].x);
-    a.idtmp[d] = a.id[t.s];
+    a.perm2[d] = a.id[t.s];
     a.celltmp[d] = c;
   });
 }
 
-// Order the particles of each cell by x, ties by caller index (deterministic).
-// A row of neighbouring cells along x is then sorted by x as a whole, which lets
-// the list build restrict each row to the window |x_j - x_i| < rl. One thread per
-// particle: its place in the cell is the number of the cell's particles with a
-// smaller key, counted over the scattered members. The first member of each cell
-// resets the cell's fill counter.
-__global__ void k_cell_rank(DevArrays a) {
+// Order the particles of each cell by x, ties by caller index (deterministic), and
+// gather each into its slot. A row of neighbouring cells along x is then sorted by
+// x as a whole, which lets the list build restrict each row to the window
+// |x_j - x_i| < rl. One thread per particle: its place in the cell is the number of
+// the cell's particles with a smaller key, counted over the scattered members. It
+// then writes the particle there: the positions straight to the arrays that only
+// the new order uses (the build-time positions and their shadows), the
+// velocities, ids and cells to scratch, which the list build copies back slot by
+// slot (copy_back_slot). Every slot of a cell holds that cell in the scratch in
+// both orders, so the ranking's reads of it need no barrier. The first member of
+// each cell resets the cell's fill counter.
+__global__ void k_cell_rank(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
     if (!t.act) return;
     const int p = t.local;           // position in the scattered order
     const int i = a.perm[t.s];       // the particle's slot before the rebuild
-    if (P.nc == 1) {
-      a.perm2[t.s] = i;
-      return;
+    int dst = p;                     // nc == 1: one cell, the scattered order is kept
+    if (P.nc > 1) {
+      const long long* key = a.skey + P.p_off;
+      const int32_t* idk = a.perm2 + P.p_off;  // caller indices in the scattered order
+      const int c = a.celltmp[t.s];
+      const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
+      if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
+      const long long ki = key[p];
+      const int32_t idi = idk[p];
+      int rank = 0;
+      for (int q = lo; q < hi; ++q) {
+        const long long kj = key[q];
+        rank += (kj < ki || (kj == ki && idk[q] < idi)) ? 1 : 0;
+      }
+      if (!check_ok(a, t.sys, lo + rank < hi, kChkRank)) return;
+      dst = lo + rank;
     }
-    const long long* key = a.skey + P.p_off;
-    const int32_t* idk = a.idtmp + P.p_off;
-    const int c = a.celltmp[t.s];
-    const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
-    if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
-    const long long ki = key[p];
-    const int32_t idi = idk[p];
-    int rank = 0;
-    for (int q = lo; q < hi; ++q) {
-      const long long kj = key[q];
-      rank += (kj < ki || (kj == ki && idk[q] < idi)) ? 1 : 0;
-    }
-    if (!check_ok(a, t.sys, lo + rank < hi, kChkRank)) return;
-    a.perm2[P.p_off + lo + rank] = i;
-  });
-}
-
-// Gather into the sorted order. The positions go straight to the arrays that
-// only the new order uses (the build-time positions and their shadows); the
-// velocities, ids and cells go to scratch, and the list build copies them (and
-// the positions) back slot by slot (copy_back_slot).
-__global__ void k_gather(DevArrays a, int cur) {
-  for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
-    if (!t.act) return;
-    const int src = a.perm2[t.s];
-    if (!check_ok(a, t.sys, src >= 0 && src < P.n, kChkGather)) return;
-    const int64_t old = P.p_off + src;
+    if (!check_ok(a, t.sys, i >= 0 && i < P.n, kChkGather)) return;
+    const int64_t old = P.p_off + i, d = P.p_off + dst;
     const double4_32a x = a.x[cur][old];
-    a.xref[t.s] = x;
+    a.xref[d] = x;
     int4 q = fixed4(x, P.qscale);
-    a.xqref[t.s] = q;
+    a.xqref[d] = q;
     q.w = __float_as_int((float)x.x);  // x as float: the list build's window key
-    a.xq[cur][t.s] = q;
-    a.xf[t.s] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
-    a.vtmp[t.s] = a.v[old];
-    a.idtmp[t.s] = a.id[old];
-    a.celltmp[t.s] = a.cell[old];
+    a.xq[cur][d] = q;
+    a.xf[d] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.0f);
+    a.vtmp[d] = a.v[old];
+    a.idtmp[d] = a.id[old];
+    a.celltmp[d] = a.cell[old];
   });
 }
 
@@ -1865,6 +1843,8 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     carry += total64_s;
     __syncthreads();
   }
+  // the pass's chunk totals start at zero (the count kernel adds to them)
+  for (int q = (int)threadIdx.x; q < (int)(carry >> 32); q += (int)blockDim.x) a.chunk_sum[q] = 0;
   if (threadIdx.x == 0) {
     const int nreb = base_s;
     reb_pref[nreb] = (int32_t)(carry & 0xffffffffll);
@@ -1910,14 +1890,14 @@ void launch_cell_count(const DevArrays& a, int cur, cudaStream_t s) {
 void launch_cell_scan(const DevArrays& a, int nreb, cudaStream_t s) {
   // blocks stride over the chunks: one wave of 8 blocks per SM at most
   const unsigned g = (unsigned)std::max(1, std::min(a.chunk_cap, 152 * 8));
-  k_cell_sums<<<g, kScanBlock, 0, s>>>(a, nreb);
   k_cell_starts<<<g, kScanBlock, 0, s>>>(a, nreb);
 }
 void launch_scatter(const DevArrays& a, int cur, cudaStream_t s) {
   k_scatter<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
 }
-void launch_cell_rank(const DevArrays& a, cudaStream_t s) { k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a); }
-void launch_gather(const DevArrays& a, int cur, cudaStream_t s) { k_gather<<<bin_blocks(a), kBlock, 0, s>>>(a, cur); }
+void launch_cell_rank(const DevArrays& a, int cur, cudaStream_t s) {
+  k_cell_rank<<<bin_blocks(a), kBlock, 0, s>>>(a, cur);
+}
 namespace {
 inline unsigned blocks_of(const DevArrays& a, int block) {
   return (unsigned)std::max<int64_t>(1, ((int64_t)a.ntiles * kTile + block - 1) / block);
