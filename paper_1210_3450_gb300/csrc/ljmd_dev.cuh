@@ -24,6 +24,9 @@ constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 
 // Cells per chunk of the two-pass cell-count scan (256 threads x 4 cells).
 constexpr int kScanChunk = 1024;
+// Copies of each chunk total that the count kernel adds to (by warp), so that its
+// atomics do not all meet on a few words; the scan sums the copies.
+constexpr int kChunkCopies = 8;
 __host__ __device__ inline int32_t scan_chunks(int64_t ncell) { return (int32_t)((ncell + kScanChunk - 1) / kScanChunk); }
 
 // Word index of list entry k of the particle in lane `lane` of local tile tl
@@ -134,7 +137,8 @@ struct DevArrays {
   const int32_t* sys_order;   // system ids by descending list-build cost per tile
   const int32_t* reb_pref;    // exclusive prefix of the rebuilding systems' tile counts (nreb + 1)
   int32_t* chunk_pref;        // exclusive prefix of the rebuilding systems' cell-chunk counts (nreb + 1)
-  int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems (summed by the count)
+  int32_t* chunk_sum;         // particles per cell chunk of the rebuilding systems, kChunkCopies partial
+                              // sums each (added up by the count)
   int32_t chunk_cap;          // entries of chunk_sum
   int32_t nreb;               // rebuilding systems (host-driven passes; the graph reads ctl->nreb)
   int32_t* tile_next;         // work counter of the list build (reset before each build)

@@ -372,7 +372,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.cstart, caps_.cells));
   // a system of ncell cells has at most ncell / kScanChunk + 1 chunks
   d_.chunk_cap = (int32_t)(caps_.cells / kScanChunk + ns + 1);
-  CKR(dmalloc(&d_.chunk_sum, d_.chunk_cap));
+  CKR(dmalloc(&d_.chunk_sum, (int64_t)d_.chunk_cap * kChunkCopies));
   CK(cudaMemset(d_.v, 0, sizeof(double4_32a) * P));
   CK(cudaMemset(d_.f, 0, sizeof(double4_32a) * P));
   CK(cudaMemset(d_.xref, 0, sizeof(double4_32a) * P));
@@ -766,7 +766,7 @@ int Engine::rebuild(std::vector<int> which, cudaStream_t s) {
     pref[nreb] = tiles;
     cpref[nreb] = chunks;
     CK(cudaMemcpyAsync(d_rebuild_, h_rebuild_, sizeof(int32_t) * (4 * nsys() + 2), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(d_.chunk_sum, 0, sizeof(int32_t) * (size_t)chunks, s));  // totalled by the count
+    CK(cudaMemsetAsync(d_.chunk_sum, 0, sizeof(int32_t) * (size_t)chunks * kChunkCopies, s));  // totalled by the count
     CK(cudaMemsetAsync(d_status_, 0, sizeof(SysStatus) * nsys(), s));
     CK(cudaMemsetAsync(&d_ctl_->next_tile, 0, sizeof(int32_t), s));
     DevArrays a = arrays();

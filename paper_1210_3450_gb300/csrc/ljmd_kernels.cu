@@ -186,7 +186,8 @@ __global__ void k_cell_count(DevArrays a, int cur) {
     if (P.nc > 1) {  // uniform over the warp
       warp_cell_add(a.ccount + P.c_off, c);
       // the scan's chunk totals (zeroed by the pass's decision), one atomic per chunk of the warp
-      warp_cell_add(a.chunk_sum, c >= 0 ? a.chunk_pref[t.r] + c / kScanChunk : -1);
+      const int copy = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) & (kChunkCopies - 1);
+      warp_cell_add(a.chunk_sum, c >= 0 ? (a.chunk_pref[t.r] + c / kScanChunk) * kChunkCopies + copy : -1);
     }
   });
 }
@@ -236,7 +237,8 @@ __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nre
     const int k = w - a.chunk_pref[r];
     // particles in the system's earlier chunks
     int off = 0;
-    for (int q = a.chunk_pref[r] + (int)threadIdx.x; q < w; q += kScanBlock) off += a.chunk_sum[q];
+    for (int q = a.chunk_pref[r] * kChunkCopies + (int)threadIdx.x; q < w * kChunkCopies; q += kScanBlock)
+      off += a.chunk_sum[q];
     off = block_sum(off, ws);
     int32_t* cnt = a.ccount + P.c_off;
     int32_t* cst = a.cstart + P.c_off;
@@ -1844,7 +1846,7 @@ __global__ void __launch_bounds__(1024) k_decide(DevArrays a, int nsys, int fp32
     __syncthreads();
   }
   // the pass's chunk totals start at zero (the count kernel adds to them)
-  for (int q = (int)threadIdx.x; q < (int)(carry >> 32); q += (int)blockDim.x) a.chunk_sum[q] = 0;
+  for (int q = (int)threadIdx.x; q < (int)(carry >> 32) * kChunkCopies; q += (int)blockDim.x) a.chunk_sum[q] = 0;
   if (threadIdx.x == 0) {
     const int nreb = base_s;
     reb_pref[nreb] = (int32_t)(carry & 0xffffffffll);
