@@ -424,6 +424,13 @@ struct ListCtx {
     if (count < kmax) *wp = e;
     advance();
   }
+  // Entries up to the next multiple of four hold the particle itself, so that the
+  // FP32 step reads whole groups of four without a bound per entry (the pair with
+  // itself has r = 0, which its force loop leaves out).
+  __device__ __forceinline__ void pad() {
+    uint32_t* w = wp;
+    for (int c = count; (c & 3) != 0 && c < kmax; ++c) *w++ = (uint32_t)li;
+  }
   // Append candidates j0 + k (image bits cbits) for the set bits k of `bits`, in
   // ascending k; the capacity is checked once for all of them.
   __device__ __forceinline__ void push_bits(unsigned bits, int j0, uint32_t cbits) {
@@ -749,6 +756,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_build_list(DevArrays a,
       if (Pp->nc == 1) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
       else lane_rows<PRE, kPrune>(a, cur, Pp, o, p_off);
     }
+    if (act) o.pad();
     list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
   }
 }
@@ -781,6 +789,7 @@ __device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int
   const int nc = Pp->nc;
   if (nc == 1) {
     if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+    if (act) o.pad();
     list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
     return;
   }
@@ -890,7 +899,8 @@ __device__ __forceinline__ void build_tile_warp(const DevArrays& a, int cur, int
       }
     }
   }
-  list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+  if (act) o.pad();
+    list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
 }
 
 }  // namespace
@@ -932,6 +942,7 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
   const int nc = Pp->nc;
   if (nc == 1) {  // uniform over the warp
     if (act) sweep_all(o, a.xq[cur] + p_off, Pp->rl2q_hi, n);
+    if (act) o.pad();
     list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
     return;
   }
@@ -1001,7 +1012,8 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
       }
     }
   }
-  list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
+  if (act) o.pad();
+    list_done(a, sys, p_off + li, o.count, kmax, act, kFull, lane);
 }
 
 }  // namespace
@@ -1081,14 +1093,15 @@ __device__ __forceinline__ void warp_max_disp(const DevArrays& a, int sys, unsig
 }
 
 // FP32 pair force from an exact fixed-point separation; returns 0 for invalid
-// slots and for r >= rc without branching (g (24 r^-8 - 48 r^-14 + 8 c2)).
+// slots, for r >= rc and for r = 0 (a list's padding entries name the particle
+// itself) without branching (g (24 r^-8 - 48 r^-14 + 8 c2)).
 __device__ __forceinline__ void pair_fp32(const int4& qi, const int4& qj, bool valid, float qu, float rc2,
                                           float c2x8, float& fx, float& fy, float& fz) {
   const float dx = (float)wrapped_diff(qj.x, qi.x) * qu;
   const float dy = (float)wrapped_diff(qj.y, qi.y) * qu;
   const float dz = (float)wrapped_diff(qj.z, qi.z) * qu;
   const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-  const bool in = valid && r2 < rc2;
+  const bool in = valid && r2 < rc2 && r2 > 0.0f;
   const float r2s = in ? r2 : 1.0f;
   float ir2;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ir2) : "f"(r2s));
@@ -1163,22 +1176,18 @@ __global__ void __launch_bounds__(BLOCK) k_step_fp32(DevArrays a, int cur, doubl
 #pragma unroll
       for (int u = 0; u < GROUPS; ++u)
         en[u] = (g + GROUPS + u < ng) ? ld_list(lp4 + (int64_t)(g + GROUPS + u) * kTile, HINT) : none;
+        // the list is padded to whole groups of four with the particle itself, and
+      // groups past its end read `none` (also the particle itself)
       int4 q[4 * GROUPS];
-      bool ok[4 * GROUPS];
 #pragma unroll
       for (int u = 0; u < GROUPS; ++u) {
-        const int rem = cnt - 4 * (g + u);
-        ok[4 * u + 0] = rem > 0;
-        ok[4 * u + 1] = rem > 1;
-        ok[4 * u + 2] = rem > 2;
-        ok[4 * u + 3] = rem > 3;
-        q[4 * u + 0] = ld_shadow(qs + (ok[4 * u + 0] ? partner_slot(a, t.sys, e[u].x, P.n, self) : self), HINT);
-        q[4 * u + 1] = ld_shadow(qs + (ok[4 * u + 1] ? partner_slot(a, t.sys, e[u].y, P.n, self) : self), HINT);
-        q[4 * u + 2] = ld_shadow(qs + (ok[4 * u + 2] ? partner_slot(a, t.sys, e[u].z, P.n, self) : self), HINT);
-        q[4 * u + 3] = ld_shadow(qs + (ok[4 * u + 3] ? partner_slot(a, t.sys, e[u].w, P.n, self) : self), HINT);
+        q[4 * u + 0] = ld_shadow(qs + partner_slot(a, t.sys, e[u].x, P.n, self), HINT);
+        q[4 * u + 1] = ld_shadow(qs + partner_slot(a, t.sys, e[u].y, P.n, self), HINT);
+        q[4 * u + 2] = ld_shadow(qs + partner_slot(a, t.sys, e[u].z, P.n, self), HINT);
+        q[4 * u + 3] = ld_shadow(qs + partner_slot(a, t.sys, e[u].w, P.n, self), HINT);
       }
 #pragma unroll
-      for (int m = 0; m < 4 * GROUPS; ++m) pair_fp32(qi, q[m], ok[m], qu, rc2, c2x8, fx, fy, fz);
+      for (int m = 0; m < 4 * GROUPS; ++m) pair_fp32(qi, q[m], true, qu, rc2, c2x8, fx, fy, fz);
 #pragma unroll
       for (int u = 0; u < GROUPS; ++u) e[u] = en[u];
     }
