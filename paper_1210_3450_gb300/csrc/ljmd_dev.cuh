@@ -124,7 +124,7 @@ struct DevArrays {
   int32_t* idtmp;
   int32_t* celltmp;
   int32_t* perm;      // scattered position -> old slot (cell order, arbitrary within a cell)
-  int32_t* perm2;     // caller index of each scattered position (the ranking's tie-break)
+  int32_t* sid;     // caller index of each scattered position (the ranking's tie-break)
   int32_t* ccount;    // particles per cell (then fill counters)
   int32_t* cstart;    // first slot of each cell (relative to the system), ncell + 1 per system
   // systems

@@ -289,7 +289,7 @@ void Engine::free_all() {
   for (int b = 0; b < 2; ++b) { dfree(d_.x[b]); dfree(d_.xq[b]); }
   dfree(d_.v); dfree(d_.xref); dfree(d_.xqref); dfree(d_.f); dfree(d_.facc); dfree(d_.id); dfree(d_.cell); dfree(d_.ncnt);
   dfree(d_.nbr); dfree(d_.tile_obs); dfree(d_.skey); dfree(d_.xf); dfree(d_.vtmp); dfree(d_.idtmp);
-  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.perm2); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
+  dfree(d_.celltmp); dfree(d_.perm); dfree(d_.sid); dfree(d_.ccount); dfree(d_.cstart); dfree(d_.chunk_sum);
   dfree(d_params_); dfree(d_status_); dfree(d_disp2_); dfree(d_margin_); dfree(d_checks_); dfree(d_rebuild_); dfree(d_order_); dfree(d_tile_sys_);
   dfree(d_obs_); dfree(d_stage_); dfree(d_pairs_); dfree(d_obs_work_); dfree(d_obs_chunk_);
   hfree(h_status_); hfree(h_disp2_); hfree(h_rebuild_); hfree(h_obs_); hfree(h_obs_work_);
@@ -367,7 +367,7 @@ int Engine::alloc_arrays() {
   CKR(dmalloc(&d_.idtmp, P));
   CKR(dmalloc(&d_.celltmp, P));
   CKR(dmalloc(&d_.perm, P));
-  CKR(dmalloc(&d_.perm2, P));
+  CKR(dmalloc(&d_.sid, P));
   CKR(dmalloc(&d_.ccount, caps_.cells));
   CKR(dmalloc(&d_.cstart, caps_.cells));
   // a system of ncell cells has at most ncell / kScanChunk + 1 chunks

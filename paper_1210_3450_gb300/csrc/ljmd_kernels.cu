@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kScanBlock) k_cell_starts(DevArrays a, int nre
 // Scatter into cell order (arbitrary within a cell). Beside the old slot, the
 // scattered position receives the particle's sort key (x, then caller index) and
 // cell, so that the ranking below reads them contiguously (the caller index goes
-// to perm2, the cell to the cell scratch).
+// to sid, the cell to the cell scratch).
 
 __global__ void k_scatter(DevArrays a, int cur) {
   for_rebuild_tiles(a, [&](const TileCtx& t, const SysParams& P) {
@@ -300,7 +300,7 @@ __global__ void k_scatter(DevArrays a, int cur) {
     a.perm[d] = t.local;
     // x >= 0 (wrapped at the count), so its bit pattern orders like the value
     a.skey[d] = __double_as_longlong(a.x[cur][t.s].x);
-    a.perm2[d] = a.id[t.s];
+    a.sid[d] = a.id[t.s];
     a.celltmp[d] = c;
   });
 }
@@ -324,7 +324,7 @@ __global__ void k_cell_rank(DevArrays a, int cur) {
     int dst = p;                     // nc == 1: one cell, the scattered order is kept
     if (P.nc > 1) {
       const long long* key = a.skey + P.p_off;
-      const int32_t* idk = a.perm2 + P.p_off;  // caller indices in the scattered order
+      const int32_t* idk = a.sid + P.p_off;  // caller indices in the scattered order
       const int c = a.celltmp[t.s];
       const int lo = a.cstart[P.c_off + c], hi = a.cstart[P.c_off + c + 1];
       if (p == lo) a.ccount[P.c_off + c] = 0;  // ready for the next binning
