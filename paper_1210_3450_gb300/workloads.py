@@ -199,12 +199,13 @@ def main(argv=None):
     p.add_argument("--drain-limit", type=float, default=None)
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     p.add_argument("--thermostat", choices=["nose-hoover", "rescale"], default="nose-hoover")
+    p.add_argument("--no-tune", action="store_true", help="batched: default launch shapes, no autotuning")
     a = p.parse_args(argv)
     from . import build
     build.build()
     prec = 1 if a.precision == "fp32" else 0
     if a.which == "batched":
-        out = batched(a.count, a.steps or 2000, precision=prec)
+        out = batched(a.count, a.steps or 2000, precision=prec, tune=not a.no_tune)
     elif a.which == "cavitation":
         out = cavitation(a.cells, a.equil_steps, steps=a.steps or 20000, precision=prec,
                          thermostat=a.thermostat)
