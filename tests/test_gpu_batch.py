@@ -68,6 +68,50 @@ def test_batch_forces_match_oracle(ljmd, oracle):
             assert np.abs(f - ref).max() / rms <= 1e-12
 
 
+def test_batch_fp32_forces_match_oracle(ljmd, oracle):
+    """FP32-force form in a batch: each system's forces within the FP32 bar (max
+    |F - F_ref| / rms F_ref <= 1e-5) of the oracle's all-pairs sum."""
+    syss = _systems()
+    with ljmd.LJBatch(systems=[(len(s["x"]), s["box"], s["rc"], s["skin"]) for s in syss],
+                      precision=ljmd.MD_FP32_FORCE) as b:
+        for k, s in enumerate(syss):
+            b.set_state(k, s["x"], s["v"])
+        for k, s in enumerate(syss):
+            f = b.forces(k)
+            ref = oracle.forces_brute(s["x"], s["box"], s["rc"])
+            rms = np.sqrt((ref ** 2).sum(1).mean())
+            assert np.abs(f - ref).max() / rms <= 1e-5
+
+
+@pytest.mark.parametrize("graph", [0, 1], ids=["host", "graph"])
+def test_system_order_does_not_change_results(ljmd, graph):
+    """Rebuild passes take the systems in descending estimated list-build cost,
+    ties by system index; that order only schedules work. The same systems placed
+    in the arena forward and reversed (two of them with equal cost, so the tie
+    order differs) end bit for bit alike."""
+    syss = _systems()
+    twin = dict(syss[0])
+    twin["v"] = li.maxwell_boltzmann(4000, 0.9, 311)   # same size and box, other velocities
+    syss.append(twin)
+    runs = []
+    for order in (list(range(len(syss))), list(reversed(range(len(syss))))):
+        with ljmd.LJBatch(systems=[(len(syss[i]["x"]), syss[i]["box"], syss[i]["rc"], syss[i]["skin"])
+                                   for i in order], precision=ljmd.MD_FP32_FORCE) as b:
+            b.set_tuning(graph=graph)
+            for k, i in enumerate(order):
+                b.set_state(k, syss[i]["x"], syss[i]["v"])
+            b.step(120, [syss[i]["dt"] for i in order])
+            got = {}
+            for k, i in enumerate(order):
+                x, v = b.get_state(k)
+                got[i] = (x, v, b.stats(k)["rebuilds"])
+            runs.append(got)
+    for i in range(len(syss)):
+        np.testing.assert_array_equal(runs[0][i][0], runs[1][i][0])
+        np.testing.assert_array_equal(runs[0][i][1], runs[1][i][1])
+        assert runs[0][i][2] == runs[1][i][2]
+
+
 def test_arena_add_remove_keeps_results(ljmd):
     """Continuous batching: B runs throughout; A leaves after 30 steps and C takes
     its place; B and C end bit-for-bit equal to their runs alone."""
