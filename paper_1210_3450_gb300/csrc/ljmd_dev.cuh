@@ -58,6 +58,7 @@ struct SysParams {
   double disp_thr;   // FP32-force form: threshold of the squared fixed-point displacement
   float rlf;         // rc + skin as float
   float csf;         // cell side L / nc as float
+  float Lf;          // L as float (the staged list build's image shifts)
   float wmargin;     // margin of the list build's geometric windows (1e-5 L + 1e-6)
   int64_t p_off;     // first slot
   int64_t c_off;     // first cell (cell arrays hold ncell + 1 entries per system)

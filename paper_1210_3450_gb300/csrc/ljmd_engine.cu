@@ -542,15 +542,18 @@ int Engine::upload_params(int only) {
     P.rl2q_hi = (float)(P.rl2 * P.qscale * P.qscale * (1.0 + 1e-5));
     P.rc2q_hi = (float)(P.rc2 * P.qscale * P.qscale * (1.0 + 1e-5));
     {
-      // Float pre-test of the list build: candidate and key positions rounded to
-      // float (error <= 2^-24 L, key shifted by an image <= 2^-23 L), so each
-      // separation errs by at most e0 = 3 u L (1 + 2^-28) plus u |d|, u = 2^-24.
+      // Float pre-test of the list build: candidate positions rounded to float
+      // (error <= u L, u = 2^-24); the particle's position shifted by an image
+      // either rounded once from the FP64 sum (error <= 2 u L) or, in the staged
+      // build, formed in float from the particle's float position and L as float
+      // (error <= 4 u L). So each separation errs by at most e0 = 5 u L (1 + 2^-28)
+      // plus u |d|.
       // Near r = rl the float r^2 then errs by less than
       //   rl^2 (2 sqrt(3) e0 / rl + 3 (e0 / rl)^2 + 6 u e0 / rl + 7 u)
       // (separation errors, three float roundings, the FP64 test's own roundings,
       // the thresholds' rounding to float); eps is twice that.
       const double u = 5.9604644775390625e-08;
-      const double g = 3.0 * u * h.spec.L * (1.0 + 3.7252902984e-09) / h.rl;
+      const double g = 5.0 * u * h.spec.L * (1.0 + 3.7252902984e-09) / h.rl;
       const double eps = 2.0 * (3.4641016151377544 * g + 3.0 * g * g + 6.0 * u * g + 7.0 * u);
       P.rl2f_lo = std::nextafter((float)(P.rl2 * (1.0 - eps)), 0.0f);
       P.rl2f_hi = std::nextafter((float)(P.rl2 * (1.0 + eps)), 3.0e38f);
@@ -567,6 +570,7 @@ int Engine::upload_params(int only) {
     P.c2f = (float)h.c2;
     P.rlf = (float)h.rl;
     P.csf = (float)(h.spec.L / h.nc);
+    P.Lf = (float)h.spec.L;
     P.wmargin = (float)(1e-5 * h.spec.L + 1e-6);
     P.p_off = h.p_off;
     P.c_off = h.c_off;

@@ -948,7 +948,6 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
   }
   const float4* __restrict__ xf = a.xf + p_off;
   const int32_t* __restrict__ cst = a.cstart + Pp->c_off;
-  const double L = Pp->L;
   const float w = Pp->rlf + Pp->wmargin;  // half-width of the x window
   PreTest<0> T;
   T.p = xf;
@@ -963,6 +962,7 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
     const int ci = a.celltmp[p_off + li];
     cx = ci % nc; cy = (ci / nc) % nc; cz = ci / (nc * nc);
   }
+  const float Lf = Pp->Lf;
 #pragma unroll 1
   for (int rowi = 0; rowi < 9; ++rowi) {
     const int oz = rowi / 3 - 1, oy = rowi % 3 - 1;
@@ -971,10 +971,13 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
     if (nz < 0) { nz += nc; shz = 2; } else if (nz >= nc) { nz -= nc; shz = 1; }
     if (ny < 0) { ny += nc; shy = 2; } else if (ny >= nc) { ny -= nc; shy = 1; }
     const int row = nc * (ny + nc * nz);
-    const double4_32a xi = o.xs[li];  // padding lanes read their zeroed slot
-    // image code 1 adds +L to x_j - x_i, code 2 adds -L: shift the particle instead
-    T.cy = (float)(shy == 1 ? xi.y - L : (shy == 2 ? xi.y + L : xi.y));
-    T.cz = (float)(shz == 1 ? xi.z - L : (shz == 2 ? xi.z + L : xi.z));
+    // the particle's float position (reloaded, an L1 hit; padding lanes read their
+    // zeroed slot), shifted in float: image code 1 adds +L to x_j - x_i, code 2
+    // adds -L, so shift the particle instead (the pre-test's error bound allows
+    // for these roundings)
+    const float4 fi = xf[li];
+    T.cy = shy == 1 ? fi.y - Lf : (shy == 2 ? fi.y + Lf : fi.y);
+    T.cz = shz == 1 ? fi.z - Lf : (shz == 2 ? fi.z + Lf : fi.z);
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
       int lo = 0, hi = 0;
@@ -992,7 +995,7 @@ __device__ __forceinline__ void build_tile_staged(const DevArrays& a, int cur, i
       }
       const bool ne = lo < hi;
       if (!__any_sync(kFull, ne)) continue;  // uniform
-      const float xw = (float)((code & 3u) == 1u ? xi.x - L : ((code & 3u) == 2u ? xi.x + L : xi.x));
+      const float xw = (code & 3u) == 1u ? fi.x - Lf : ((code & 3u) == 2u ? fi.x + Lf : fi.x);
       const int u0 = __reduce_min_sync(kFull, ne ? lo : 0x7fffffff);
       const int u1 = __reduce_max_sync(kFull, ne ? hi : -1);
       if (u1 - u0 <= kStage) {

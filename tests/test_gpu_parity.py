@@ -88,7 +88,7 @@ def shell_pairs(count=2000, box=300.0, rl=2.8, seed=11):
 
 # L = 300, and L = 430, the box of the largest system the library takes
 # (N = 2^26 - 1 at rho 0.8442), where the float pre-test's shell is widest
-# (+-9.6e-5 of rl against +-6.7e-5 at L = 300; the pairs span +-4e-4)
+# (+-1.6e-4 of rl against +-1.1e-4 at L = 300; the pairs span +-4e-4)
 _S = {300: shell_pairs(), 430: shell_pairs(box=430.0, seed=12)}
 
 
