@@ -1063,21 +1063,23 @@ __device__ __forceinline__ unsigned long long integrate(const DevArrays& a, cons
     return ~0ull;
   }
   // velocity-bound rule: |v|^2 of the drift velocity, (vx vx + vy vy) + vz vz unfused
-  const unsigned long long v2b =
-      (unsigned long long)__double_as_longlong(__dadd_rn(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)),
-                                                         __dmul_rn(v.z, v.z)));
+  // (FP64 work only under that rule)
+  auto v2b = [&v]() -> unsigned long long {
+    return (unsigned long long)__double_as_longlong(
+        __dadd_rn(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)), __dmul_rn(v.z, v.z)));
+  };
   if (kFP32) {
     // check in fixed point: exact integer squared displacement of the shadow
     const int4 q = fixed4(xn, P.qscale);
     a.xq[cur ^ 1][t.s] = q;
+    if (flags & kStepVmax) return v2b();
     const int4 r = a.xqref[t.s];
     const long long ex = wrapped_diff(q.x, r.x), ey = wrapped_diff(q.y, r.y), ez = wrapped_diff(q.z, r.z);
-    if (flags & kStepVmax) return v2b;
     return (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey) + (unsigned long long)(ez * ez);
   }
   // the fixed-point shadow, which the FP64 force loop's pre-classification reads
   a.xq[cur ^ 1][t.s] = fixed4(xn, P.qscale);
-  if (flags & kStepVmax) return v2b;
+  if (flags & kStepVmax) return v2b();
   // exact FP64 check, the same operations as the reference
   const double4_32a r = a.xref[t.s];
   const double ex = __dsub_rn(xn.x, r.x), ey = __dsub_rn(xn.y, r.y), ez = __dsub_rn(xn.z, r.z);
